@@ -1,0 +1,397 @@
+"""Benchmark: segment / triangle-mesh intersection on GB300.
+
+Headline workload (one step): LBVH build + boolean traversal of 10M segments
+against a 123x123 heightfield (29,768 triangles) -- the paper's 10M rays x
+~30k triangles (Table 3) with synthetic data.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--quick]
+
+Under torchrun each rank runs the same per-rank workload on its own GPU
+(segments drawn from a per-rank seed, the mesh replicated), no collective on
+the data path; value = all ranks' segments / max-over-ranks time (weak
+scaling).  --impl reference times the FP64 CPU oracle (the only baseline that
+exists: the paper's code and data are not available) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Msegments/s (build+traverse) at 10M×30k tris; fwd+bwd and batched Mseg/s"
+UNIT = "Msegments/s"
+WORKLOAD = "heightfield 123x123 (29,768 tris) x 10M segments, boolean, build+traverse"
+BYTES_PER_SEG_BOOL = 25     # 24 B of segment endpoints in + 1 B flag out
+BYTES_PER_SEG_NEAREST = 64  # 24 B in + tri, t, u, v, point, dist (40 B) out
+BYTES_PER_SEG_COUNT = 28
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def timed(fn, steps, stream, torch):
+    """Run fn() `steps` times between CUDA events on `stream`; returns ms/step."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def cpu_oracle_rate(mesh, seg, target_s=12.0, max_n=2_000_000):
+    """The FP64 oracle (CPU BVH + Moller-Trumbore, OpenMP over all host
+    cores) on a bounded sample of the segments: build + query.
+    Returns (Mseg/s, threads, sample size, seconds)."""
+    import oracle
+    threads = oracle.num_threads()
+    n = 20000
+    total = 0.0
+    while True:
+        t0 = time.perf_counter()
+        bvh = oracle.CpuBVH(mesh.V, mesh.T)
+        bvh.query(seg.A[:n], seg.B[:n], threads=threads)
+        dt = time.perf_counter() - t0
+        total += dt
+        if dt >= target_s or n >= max_n or total > 3 * target_s:
+            return n / dt / 1e6, threads, n, dt
+        n = min(max_n, int(n * max(2.0, min(20.0, target_s / max(dt, 1e-3)))))
+
+
+# ------------------------------------------------------------------ arms
+def run_ours(args):
+    import torch
+    import paper_2209_02878_gb300 as rsi
+    from paper_2209_02878_gb300 import synth
+
+    rank, local, world = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    n_seg = 10_000_000
+    mesh, seg = synth.workload_paper_bool(seed=1 + 1000 * rank, n_seg=n_seg)
+    V = torch.from_numpy(mesh.V).to(dev)
+    T = torch.from_numpy(mesh.T).to(dev)
+    A = torch.from_numpy(seg.A).to(dev)
+    B = torch.from_numpy(seg.B).to(dev)
+    flag = torch.empty(n_seg, dtype=torch.uint8, device=dev)
+    out = {"flag": flag}
+    torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        bvh = rsi.BVH(V, T, stream=stream)
+        kernels_per_step = 2 + 3 * 4 + 1 + 1 + 1 + 1  # build (17) + traversal (1)
+
+        def step():
+            bvh.build(V, T, stream=stream)
+            bvh.intersect(A, B, "bool", out=out, stream=stream)
+
+        for _ in range(max(args.warmup, 3)):
+            step()
+        stream.synchronize()
+        if bvh.status(stream) != 0:
+            raise RuntimeError("device status set during warm-up")
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            ms_step = timed(step, args.steps, stream, torch)
+            torch.cuda.synchronize()
+        if dist:
+            t = torch.tensor([ms_step], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_step = float(t.item())
+            dist.barrier()
+
+        # kernel-only timings (same stream, after the headline region)
+        ms_trav = timed(lambda: bvh.intersect(A, B, "bool", out=out, stream=stream),
+                        args.steps, stream, torch)
+        ms_build = timed(lambda: bvh.build(V, T, stream=stream), args.steps, stream, torch)
+        stats = bvh.intersect(A, B, "bool", stats=True, stream=stream)["stats"]
+
+        # end to end through the public API from pinned host memory
+        hA = torch.from_numpy(seg.A).pin_memory()
+        hB = torch.from_numpy(seg.B).pin_memory()
+        hflag = torch.empty(n_seg, dtype=torch.uint8).pin_memory()
+        dA = torch.empty_like(A)
+        dB = torch.empty_like(B)
+
+        def e2e_step():
+            dA.copy_(hA, non_blocking=True)
+            dB.copy_(hB, non_blocking=True)
+            bvh.build(V, T, stream=stream)
+            bvh.intersect(dA, dB, "bool", out=out, stream=stream)
+            hflag.copy_(flag, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        stream.synchronize()
+        ms_e2e = timed(e2e_step, max(2, args.steps // 2), stream, torch)
+
+    extras = {}
+    if not args.quick:
+        extras = run_extras(args, torch, rsi, synth, dev, stream)
+
+    peak, peak_kind = measured_peaks()
+    algo_bytes = BYTES_PER_SEG_BOOL * n_seg
+    achieved = algo_bytes / (ms_trav * 1e-3) / 1e9
+    res = {
+        "metric": METRIC, "value": round(world * n_seg / (ms_step * 1e-3) / 1e6, 3),
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (FP64 for decisions the FP32 bound cannot settle)",
+        "data": "synthetic (seeded heightfield + random-direction segments)",
+        "config": {"workload": WORKLOAD, "n_triangles": mesh.n_tri, "segments_per_gpu": n_seg,
+                   "parallelism": f"replicas x{world}, segments sharded per rank",
+                   "l2": "inputs larger than L2 (240 MB of segments per step)",
+                   "launch": "persistent grid from occupancy, block 256, stack 64, 511 smem nodes"},
+        "e2e": {"value": round(world * n_seg / (ms_e2e * 1e-3) / 1e6, 3), "unit": UNIT,
+                "h2d_bytes_per_step": 24 * n_seg, "d2h_bytes_per_step": n_seg,
+                "ms_per_step": round(ms_e2e, 4)},
+        "gpu_launches": kernels_per_step * args.steps,
+        "clocks": clk.summary(),
+        "roofline": {"bound": "hbm", "kernel": "k_trace<BOOL>", "achieved": round(achieved, 2),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 5),
+                     "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": algo_bytes,
+                     "kernel_ms": round(ms_trav, 4)},
+        "breakdown": {"traverse_only_Msegs": round(n_seg / (ms_trav * 1e-3) / 1e6, 3),
+                      "build_ms": round(ms_build, 4), "traverse_ms": round(ms_trav, 4),
+                      "node_visits_per_seg": round(stats["node_visits"] / n_seg, 3),
+                      "tri_tests_per_seg": round(stats["tri_tests"] / n_seg, 3),
+                      "fp64_tests_per_seg": stats["fp64_tests"] / n_seg},
+    }
+    res.update(extras)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, thr, n, dt = cpu_oracle_rate(mesh, seg)
+        res["cpu_baseline"] = {"value": round(rate, 5), "unit": UNIT, "cores": thr,
+                               "kind": "oracle",
+                               "sample": f"first {n} of the 10M segments, CPU BVH build + "
+                                         f"FP64 query, {dt:.1f} s"}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res))
+
+
+def run_extras(args, torch, rsi, synth, dev, stream):
+    """fwd+bwd (131k-triangle heightfield, 262k segments), count + nearest
+    (1.3M-triangle icosphere, 1M segments) and the 64-mesh batch, each beside
+    the plain single-mesh forward on the same mesh."""
+    out = {}
+    steps = max(3, args.steps)
+    with torch.cuda.stream(stream):
+        # fwd + bwd
+        mesh, seg, w = synth.workload_diff()
+        V = torch.from_numpy(mesh.V).to(dev)
+        T = torch.from_numpy(mesh.T).to(dev)
+        A = torch.from_numpy(seg.A).to(dev)
+        B = torch.from_numpy(seg.B).to(dev)
+        W = torch.from_numpy(w).to(dev)
+        bvh = rsi.BVH(V, T, stream=stream)
+
+        def fwd():
+            return bvh.intersect(A, B, "nearest", stream=stream)
+
+        def fwd_bwd():
+            bvh.build(V, T, stream=stream)
+            o = bvh.intersect(A, B, "nearest", stream=stream)
+            rsi.intersect_backward(V, T, A, B, o["tri"], o["tuv"], grad_point=W, stream=stream)
+
+        for _ in range(3):
+            fwd_bwd()
+        ms_fb = timed(fwd_bwd, steps, stream, torch)
+        ms_f = timed(lambda: (bvh.build(V, T, stream=stream), fwd()), steps, stream, torch)
+        out["fwd_bwd"] = {"workload": "heightfield 257x257 (131,072 tris) x 262,144 near-vertical "
+                                      "segments, nearest + adjoint, build included",
+                          "value": round(seg.n / (ms_fb * 1e-3) / 1e6, 3), "unit": UNIT,
+                          "forward_only": round(seg.n / (ms_f * 1e-3) / 1e6, 3)}
+        del bvh
+        # count + nearest on the big sphere
+        mesh, seg = synth.workload_sphere()
+        V = torch.from_numpy(mesh.V).to(dev)
+        T = torch.from_numpy(mesh.T).to(dev)
+        A = torch.from_numpy(seg.A).to(dev)
+        B = torch.from_numpy(seg.B).to(dev)
+        bvh = rsi.BVH(V, T, stream=stream)
+        res = {}
+        for mode in ("bool", "count", "nearest"):
+            o = bvh.intersect(A, B, mode, stream=stream)
+            ms = timed(lambda: bvh.intersect(A, B, mode, out=o, stream=stream), steps, stream,
+                       torch)
+            res[mode] = round(seg.n / (ms * 1e-3) / 1e6, 3)
+        ms_b = timed(lambda: bvh.build(V, T, stream=stream), steps, stream, torch)
+        out["sphere"] = {"workload": "icosphere L8 (1,310,720 tris) x 1M segments in a cube",
+                         "traverse_Msegs": res, "build_ms": round(ms_b, 3), "unit": UNIT}
+        del bvh
+        # batched
+        items = synth.workload_batched()
+        tens = [(torch.from_numpy(m.V).to(dev), torch.from_numpy(m.T).to(dev),
+                 torch.from_numpy(s.A).to(dev), torch.from_numpy(s.B).to(dev), mode)
+                for m, s, mode in items]
+        n_total = sum(s.n for _, s, _ in items)
+        batch = rsi.Batch(tens, stream=stream)
+        batch.run_graph(rebuild=True, stream=stream)
+        stream.synchronize()
+        ms_bt = timed(lambda: batch.run_graph(rebuild=True, stream=stream), steps, stream, torch)
+        bvhs = [rsi.BVH(t[0], t[1], stream=stream) for t in tens]
+        outs = [bv.intersect(t[2], t[3], t[4], stream=stream) for bv, t in zip(bvhs, tens)]
+
+        def singles():
+            for bv, t, o in zip(bvhs, tens, outs):
+                bv.build(t[0], t[1], stream=stream)
+                bv.intersect(t[2], t[3], t[4], out=o, stream=stream)
+
+        singles()
+        ms_single = timed(singles, steps, stream, torch)
+        out["batched"] = {"workload": f"64 meshes (1k-200k tris), {n_total} segments, "
+                                      "bool/nearest alternating, one graph: build + persistent "
+                                      "traversal",
+                          "value": round(n_total / (ms_bt * 1e-3) / 1e6, 3), "unit": UNIT,
+                          "per_mesh_launches": round(n_total / (ms_single * 1e-3) / 1e6, 3)}
+        batch.close()
+    return out
+
+
+def run_reference(args):
+    """The FP64 CPU oracle timed on the host cores, same metric and workload,
+    each step a bounded sample of the 10M segments (build + query)."""
+    rank, _, world = env_rank()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2209_02878_gb300 import synth
+    oracle.compile_oracle()
+    n_sample = 100_000
+    mesh, seg = synth.workload_paper_bool(n_seg=n_sample * max(1, args.steps))
+    threads = oracle.num_threads()
+
+    def step(k):
+        s = slice(k * n_sample, (k + 1) * n_sample)
+        bvh = oracle.CpuBVH(mesh.V, mesh.T)
+        bvh.query(seg.A[s], seg.B[s], threads=threads)
+
+    for _ in range(max(args.warmup, 3)):
+        step(0)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(k)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = round(n_sample / dt / 1e6, 5)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step": n_sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{n_sample} segments per step (CPU BVH build + FP64 query)"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="headline workload only")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,329 @@
+/*
+ * rsi.h -- C ABI of librsi: line-segment / triangle-mesh intersection on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: arXiv 2209.02878 (Leung, "GPU implementation of a ray-surface
+ * intersection algorithm in CUDA").  The problem (Sec. 1): N_r segments
+ * l_i = (r_start_i, r_end_i) against a mesh of N_t triangles t_j indexing
+ * vertices V; result per segment is a crossing flag (default), a crossing
+ * count (Sec. 2.4 "intercept_count") or the intersecting point and triangle
+ * (Sec. 2.4 "barycentric").  The segment/triangle predicate is
+ * Moller-Trumbore (Sec. 2); the acceleration structure is a linear BVH over
+ * Morton-sorted triangle centroids (Sec. 2: centroids, quantisation, Morton
+ * codes, sort, binary radix tree, bottom-up boxes) searched per segment with
+ * a stack (Sec. 3.2, bvhTraverse / bvhFindCollisions).
+ *
+ * Conventions shared by every call:
+ *  - Layouts follow Sec. 2.5: vertices float32 [nV][3], triangles int32
+ *    [nT][3] (0-based vertex indices), segment starts / ends float32 [nR][3],
+ *    all C-contiguous, x y z interleaved.
+ *  - Pointers named d* are DEVICE pointers of the current CUDA device; the
+ *    caller owns them, must keep them alive until the stream work using them
+ *    has finished, and the library never frees them.  Pointers without the d
+ *    prefix are host pointers.
+ *  - rsi_stream is a cudaStream_t (NULL = legacy default stream).  Every
+ *    compute call is asynchronous on that stream unless stated otherwise.
+ *  - Calls never throw, never abort and never trap the GPU; they return an
+ *    rsi_status.  Errors that can only be seen on the device (a triangle index
+ *    outside [0, nV)) are latched in a device status word and returned by
+ *    rsi_bvh_status (which synchronises the stream).
+ *  - Arithmetic: FP32 with certified error bounds; every boolean decision
+ *    whose FP32 error bound does not settle it is recomputed in FP64 in the
+ *    exact operation order of the definition below, so flags, counts and
+ *    triangle ids equal those of the FP64 definition.
+ *
+ * Definition computed (Sec. 2, Moller-Trumbore without division):
+ *   d = b - a, e1 = v1 - v0, e2 = v2 - v0, p = d x e2, det = e1.p,
+ *   s0 = a - v0, q = s0 x e1, nU = s0.p, nV = d.q, nT = e2.q;
+ *   if det < 0 negate det, nU, nV, nT;
+ *   hit <=> det > 0, nU >= 0, nV >= 0, nU + nV <= det, 0 <= nT <= det;
+ *   t = nT/det, u = nU/det, v = nV/det, P = a + t d, dist = t |d|.
+ *   A segment or triangle with a non-finite coordinate never hits.
+ */
+#ifndef RSI_H
+#define RSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* rsi_stream; /* == cudaStream_t */
+typedef struct rsi_bvh_s* rsi_bvh;      /* opaque, library-owned */
+typedef struct rsi_batch_s* rsi_batch;  /* opaque, library-owned */
+
+typedef enum {
+    RSI_OK = 0,
+    RSI_ERR_ARG = 1,            /* invalid argument (null, negative size, bad mode) */
+    RSI_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    RSI_ERR_OOM = 3,            /* device allocation failed */
+    RSI_ERR_BAD_INDEX = 4,      /* a triangle index is outside [0, nV) */
+    RSI_ERR_STACK_OVERFLOW = 5, /* traversal stack too small (never with depth >= 64) */
+    RSI_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+    RSI_ERR_NOT_BUILT = 7       /* handle has no built tree */
+} rsi_status;
+
+typedef enum {
+    RSI_MODE_BOOL = 0,    /* Sec. 1: crossing flag y_i in {0,1} */
+    RSI_MODE_COUNT = 1,   /* Sec. 2.4 intercept_count: number of crossings */
+    RSI_MODE_NEAREST = 2  /* Sec. 2.4 barycentric: nearest crossing (min t,
+                             ties to the lower triangle index) */
+} rsi_mode;
+
+/* Options fixed when a tree is built.  Zero-initialised = defaults. */
+typedef struct {
+    int32_t leaf_size;  /* max triangles per leaf, 1..8 (0 -> 1, the paper's
+                           one-triangle leaves, Sec. 3.1) */
+    int32_t top_levels; /* breadth-first levels of the tree copied into a
+                           compact top "treelet" that traversal can stage in
+                           shared memory, 0..12 (0 -> 10; -1 -> no treelet) */
+} rsi_build_opts;
+
+/* Options of one traversal launch.  Zero-initialised = defaults. */
+typedef struct {
+    int32_t block_size;  /* threads per block, multiple of 32 in [32, 1024]
+                            (0 -> 256) */
+    int32_t stack_depth; /* per-segment traversal stack entries: 16, 32 or 64
+                            (0 -> 64).  Radix trees over 64-bit keys are at
+                            most 63 levels deep, so 64 never overflows; a
+                            smaller stack re-runs overflowed segments with a
+                            deeper one. */
+    int32_t smem_nodes;  /* treelet nodes staged in shared memory per block
+                            (64 B each, at most 2048); 0 -> automatic (511);
+                            -1 -> none */
+    int32_t stats;       /* nonzero: count node visits, triangle tests and
+                            FP64 fallbacks (slower; see rsi_get_stats) */
+} rsi_launch_opts;
+
+/* Per-segment outputs, all DEVICE pointers owned by the caller.  Which must be
+ * non-NULL depends on the mode; the others may be NULL and are ignored.
+ *   BOOL:    flag  uint8[nR]   (1 = the segment crosses the surface)
+ *   COUNT:   count int32[nR]   (number of triangles crossed)
+ *   NEAREST: tri   int32[nR]   (original triangle index, -1 = no crossing)
+ *            tuv   float[nR][3] (t, u, v; 0 on a miss)      optional
+ *            point float[nR][3] (a + t d; 0 on a miss)       optional
+ *            dist  float[nR]    (t |b - a|; 0 on a miss)     optional
+ * Compaction (COUNT and NEAREST; optional): when hit_idx != NULL, the index
+ * of every segment with at least one crossing is appended to hit_idx[0..cap)
+ * by a warp-aggregated atomic; *n_hits (device int64, zeroed by the call)
+ * receives the total, which may exceed cap (entries past cap are dropped).
+ * Order across warps is unspecified; for NEAREST the parallel arrays
+ * hit_tri / hit_dist / hit_point, and for COUNT hit_count, are filled at the
+ * same positions when non-NULL (the paper's (intersecting_rays, distances,
+ * intersecting_triangles, intersecting_points), Sec. 2.4). */
+typedef struct {
+    uint8_t* flag;
+    int32_t* count;
+    int32_t* tri;
+    float* tuv;
+    float* point;
+    float* dist;
+    int32_t* hit_idx;
+    int64_t hit_cap;
+    int64_t* n_hits;
+    int32_t* hit_tri;
+    float* hit_dist;
+    float* hit_point;
+    int32_t* hit_count;
+} rsi_output;
+
+typedef struct {
+    int64_t n_vertices;
+    int64_t n_triangles;
+    int32_t leaf_size;
+    int32_t treelet_nodes;  /* nodes in the breadth-first top treelet */
+    int64_t device_bytes;   /* device memory held by the handle */
+} rsi_bvh_info;
+
+typedef struct {
+    int64_t segments;
+    int64_t node_visits;   /* internal nodes fetched */
+    int64_t tri_tests;     /* FP32 segment/triangle tests */
+    int64_t fp64_tests;    /* tests decided by the FP64 recomputation */
+    int64_t fp64_refines;  /* nearest hits whose outputs were refined in FP64 */
+    int64_t overflows;     /* segments re-run with a deeper stack */
+} rsi_stats;
+
+/* Library and status helpers. */
+const char* rsi_version(void);
+const char* rsi_status_string(rsi_status s);
+
+/* ---------------------------------------------------------------- BVH --- */
+
+/* Allocate a handle for meshes of nV vertices and nT triangles (device memory
+ * from cudaMallocAsync on stream s, ordered on s).  No tree is built yet.
+ * Sec. 2 / Sec. 3.1: the paper's internalNodes (N_t - 1) and leafNodes (N_t)
+ * arrays; here one 64-byte node per internal node holding both child boxes,
+ * plus a root slot, and the triangles re-stored in leaf order.
+ * Errors: RSI_ERR_ARG (nV < 0, nT < 0, nT >= 2^31, out == NULL, bad opts),
+ * RSI_ERR_OOM. */
+rsi_status rsi_bvh_create(int64_t nV, int64_t nT, const rsi_build_opts* opt,
+                          rsi_stream s, rsi_bvh* out);
+
+/* Build the LBVH of (dV, dT) into h, asynchronously on s, without allocating
+ * (capturable in a CUDA graph).  Steps (Sec. 2): centroid support interval,
+ * 10-bit-per-axis quantisation and 30-bit Morton codes, on-device radix sort,
+ * Karras binary radix tree, bottom-up boxes merged with per-node atomics
+ * (Sec. 3.1 `atomic` field), optional leaf collapse and the top treelet.
+ * dV float32[nV][3], dT int32[nT][3] with the sizes given at create time.
+ * Index errors are latched for rsi_bvh_status.  Errors: RSI_ERR_ARG,
+ * RSI_ERR_CUDA. */
+rsi_status rsi_bvh_build(rsi_bvh h, const float* dV, const int32_t* dT, rsi_stream s);
+
+/* rsi_bvh_create followed by rsi_bvh_build. */
+rsi_status rsi_build_bvh(const float* dV, int64_t nV, const int32_t* dT, int64_t nT,
+                         const rsi_build_opts* opt, rsi_stream s, rsi_bvh* out);
+
+/* Re-fit the boxes of a built tree to new vertex positions dV (same nV, same
+ * triangles as the last build): the bottom-up box pass of Sec. 2 without the
+ * sort and hierarchy steps.  Results stay exact; only traversal speed depends
+ * on how far the vertices moved.  Asynchronous, no allocation.  dT must be
+ * the triangle array of the last build.  Errors: RSI_ERR_ARG,
+ * RSI_ERR_NOT_BUILT, RSI_ERR_CUDA. */
+rsi_status rsi_refit(rsi_bvh h, const float* dV, const int32_t* dT, rsi_stream s);
+
+/* Synchronise s and return the device-side status latched by builds and
+ * traversals on h since the last call (RSI_OK, RSI_ERR_BAD_INDEX,
+ * RSI_ERR_STACK_OVERFLOW), then clear it. */
+rsi_status rsi_bvh_status(rsi_bvh h, rsi_stream s);
+
+rsi_status rsi_bvh_get_info(rsi_bvh h, rsi_bvh_info* info);
+
+/* Free a handle (stream-ordered on the stream of its last build). */
+rsi_status rsi_bvh_destroy(rsi_bvh h);
+
+/* Debug / validation: synchronise s and copy the tree of h to HOST buffers,
+ * each NULL-able:
+ *   bounds  float[6]        centroid support interval (lo xyz, hi xyz)
+ *   codes   uint32[nT]      Morton codes in sorted (leaf) order
+ *   order   int32[nT]       sorted position -> original triangle index
+ *   left, right int32[nT-1] children of Karras internal node i: >= 0 internal
+ *                           node, < 0 leaf -(pos+1)
+ *   range   int32[nT-1][2]  first, last leaf of internal node i
+ *   nbox    float[nT-1][6]  internal node boxes (lo xyz, hi xyz)
+ *   lbox    float[nT][6]    leaf (triangle) boxes by sorted position
+ *   nodes   float[nT][16]   the traversal nodes (slot nT-1 is the root slot):
+ *                           child0 lo.xyz, child0 hi.x | child0 hi.yz,
+ *                           child1 lo.xy | child1 lo.z, child1 hi.xyz |
+ *                           ref0, ref1, cnt0, cnt1 (int32 bit patterns) */
+rsi_status rsi_bvh_export(rsi_bvh h, rsi_stream s, float* bounds, uint32_t* codes,
+                          int32_t* order, int32_t* left, int32_t* right, int32_t* range,
+                          float* nbox, float* lbox, float* nodes);
+
+/* ---------------------------------------------------------- traversal --- */
+
+/* Test nR segments (dA[i] -> dB[i]) against the tree in h (Sec. 3.2-3.3,
+ * bvhIntersectionKernel): one persistent launch with warp-granular dynamic
+ * work distribution, stack traversal testing both child boxes of each node
+ * with a conservative slab test, triangles tested inline at the leaves.
+ * BOOL stops at the first crossing (Sec. 3.2, detected[rayIdx]); COUNT visits
+ * every candidate; NEAREST prunes boxes beyond the best crossing so far.
+ * out: see rsi_output.  lo: NULL = defaults.  nR == 0 is a no-op; an empty
+ * mesh gives all misses.  Errors: RSI_ERR_ARG (null required output, bad
+ * mode or options), RSI_ERR_NOT_BUILT, RSI_ERR_CUDA. */
+rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR,
+                         rsi_mode mode, const rsi_output* out,
+                         const rsi_launch_opts* lo, rsi_stream s);
+
+/* Like rsi_intersect with lo->stats set; synchronises s and returns the
+ * counters of that launch in *st (host). */
+rsi_status rsi_intersect_stats(rsi_bvh h, const float* dA, const float* dB, int64_t nR,
+                               rsi_mode mode, const rsi_output* out,
+                               const rsi_launch_opts* lo, rsi_stream s, rsi_stats* st);
+
+/* ----------------------------------------------------------- backward --- */
+
+/* Adjoint of the NEAREST outputs with the crossing triangle held fixed (not
+ * in the paper; implicit differentiation of a + t d = v0 + u e1 + v e2).
+ * With M = [-d, e1, e2], x = (t,u,v), g_x = (gt + gP.d, gu, gv),
+ * lambda = M^-T g_x:
+ *   dA[i] = (1-t)(gP + lambda),  dB[i] = t (gP + lambda),
+ *   dGradV[T[j][0]] += -(1-u-v) lambda, dGradV[T[j][1]] += -u lambda,
+ *   dGradV[T[j][2]] += -v lambda   (atomic scatter-add),
+ * and zero for segments with dTri[i] < 0.
+ * Inputs: dV, dT as for the build; dA, dB the segments; dTri int32[nR] and
+ * dTuv float[nR][3] saved from the NEAREST forward; dGradPoint float[nR][3]
+ * and dGradTuv float[nR][3] (either may be NULL = zero).  Outputs:
+ * dGradV float[nV][3] ACCUMULATED into (caller zeroes it), dGradA / dGradB
+ * float[nR][3] overwritten (either may be NULL).  Errors: RSI_ERR_ARG,
+ * RSI_ERR_CUDA; a dTri entry >= nT or a vertex index outside [0, nV) is
+ * skipped. */
+rsi_status rsi_intersect_backward(const float* dV, int64_t nV, const int32_t* dT, int64_t nT,
+                                  const float* dA, const float* dB, int64_t nR,
+                                  const int32_t* dTri, const float* dTuv,
+                                  const float* dGradPoint, const float* dGradTuv,
+                                  float* dGradV, float* dGradA, float* dGradB,
+                                  rsi_stream s);
+
+/* ------------------------------------------------------------ batched --- */
+
+/* One independent problem of a batch: a mesh, its segments, a mode and the
+ * outputs (same meaning as for rsi_intersect).  Device pointers. */
+typedef struct {
+    const float* dV;
+    int64_t nV;
+    const int32_t* dT;
+    int64_t nT;
+    const float* dA;
+    const float* dB;
+    int64_t nR;
+    int32_t mode;   /* rsi_mode */
+    int32_t pad;
+    rsi_output out;
+} rsi_batch_item;
+
+/* Plan a batch of n items (host array, copied): allocates one concatenated
+ * tree storage for all meshes and a work list of (item, segment chunk) tiles
+ * ordered by estimated cost (N_r log N_t), largest first.  The item pointers
+ * are stored: they must stay valid for the plan's lifetime.
+ * Errors: RSI_ERR_ARG, RSI_ERR_OOM, RSI_ERR_CUDA. */
+rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n,
+                            const rsi_build_opts* bo, const rsi_launch_opts* lo,
+                            rsi_stream s, rsi_batch* out);
+
+/* Build every mesh of the batch: the same build steps as rsi_bvh_build run
+ * once over all meshes (segmented by a mesh id in the sort key).
+ * Asynchronous, no allocation, capturable. */
+rsi_status rsi_batch_build(rsi_batch b, rsi_stream s);
+
+/* Traverse every item in ONE persistent launch (tiles pulled from an atomic
+ * work counter, per-tile mode).  Asynchronous, no allocation, capturable. */
+rsi_status rsi_batch_intersect(rsi_batch b, rsi_stream s);
+
+/* Capture build + intersect of the batch into a CUDA graph once (on s) and
+ * launch it; later calls replay the graph.  rebuild = 0 replays only the
+ * traversal graph. */
+rsi_status rsi_batch_run_graph(rsi_batch b, int32_t rebuild, rsi_stream s);
+
+rsi_status rsi_batch_destroy(rsi_batch b);
+
+/* -------------------------------------------------------------- tuning --- */
+
+/* One timed configuration of the tuner. */
+typedef struct {
+    int32_t block_size, stack_depth, smem_nodes, leaf_size;
+    float ms;  /* median traversal time of `reps` launches */
+} rsi_tune_entry;
+
+/* Autotuner: for every combination of the candidate lists (leaf sizes need a
+ * rebuild of h with those options), time `reps` traversals of the given
+ * segments in `mode` with CUDA events on s, write up to cap entries to
+ * table (host) and the fastest launch options / leaf size to *best_lo /
+ * *best_leaf.  The handle is left built with the best leaf size.  dV, dT
+ * must be the mesh h was built from.  Synchronous. */
+rsi_status rsi_autotune(rsi_bvh h, const float* dV, const int32_t* dT,
+                        const float* dA, const float* dB, int64_t nR, rsi_mode mode,
+                        const rsi_output* out,
+                        const int32_t* block_sizes, int32_t n_bs,
+                        const int32_t* stack_depths, int32_t n_sd,
+                        const int32_t* smem_nodes, int32_t n_sm,
+                        const int32_t* leaf_sizes, int32_t n_ls, int32_t reps,
+                        rsi_stream s, rsi_tune_entry* table, int32_t cap,
+                        int32_t* n_written, rsi_launch_opts* best_lo, int32_t* best_leaf);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSI_H */

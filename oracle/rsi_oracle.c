@@ -31,6 +31,9 @@
  *   nearest mode  : argmin_j t_ij over hits, ties to the smaller j, with
  *                   (j, t, u, v, P, dist)                (Sec. 2.4 barycentric)
  *
+ *   A segment or triangle with a non-finite coordinate never hits (the paper
+ *   is silent; without this rule infinities give hits with t = NaN).
+ *
  *   near-degenerate segment: some triangle with det != 0 has
  *   m = min(u, v, 1-u-v, t, 1-t) in [-1e-6, 1e-6], or the segment is exactly
  *   parallel to and coplanar with a triangle whose box it touches.
@@ -153,8 +156,15 @@ static void acc_init(acc_t* s) {
     s->neardeg = 0;
 }
 
+static int finite3(const double* x) {
+    return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
+}
+
 static void acc_add(acc_t* s, const double* a, const double* b, const double* v0,
                     const double* v1, const double* v2, long j) {
+    /* a segment or triangle with a non-finite coordinate never hits */
+    if (!finite3(a) || !finite3(b) || !finite3(v0) || !finite3(v1) || !finite3(v2))
+        return;
     mt_t r;
     mt_test(a, b, v0, v1, v2, &r);
     if (r.det != 0.0) {

@@ -1,0 +1,724 @@
+// C ABI of librsi (declarations and documentation in include/rsi.h).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "rsi.h"
+#include "rsi_build.h"
+#include "rsi_trace.h"
+
+using rsi::MeshArgs;
+using rsi::MeshDesc;
+using rsi::TreeBufs;
+
+#define RSI_CK(call)                                                                   \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            cudaGetLastError();                                                        \
+            return e_ == cudaErrorMemoryAllocation ? RSI_ERR_OOM : RSI_ERR_CUDA;       \
+        }                                                                              \
+    } while (0)
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr int kDefaultSmemNodes = 511;  // 32 KB of treelet per block
+
+// Carves the device buffers of a tree over N triangles and M meshes out of
+// one allocation.  With base == nullptr only the total size is computed.
+size_t carve(TreeBufs& tb, int64_t N, int M, int nblk, char* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += align256(bytes > 0 ? bytes : 1);
+        return p;
+    };
+    const int64_t n1 = N > 0 ? N : 1;
+    tb.N = (int32_t)N;
+    tb.M = M;
+    tb.ntiles = (int32_t)((N + rsi::kSortTile - 1) / rsi::kSortTile);
+    tb.nblk = nblk;
+    tb.keys[0] = (uint64_t*)take(8 * n1);
+    tb.keys[1] = (uint64_t*)take(8 * n1);
+    tb.vals[0] = (uint32_t*)take(4 * n1);
+    tb.vals[1] = (uint32_t*)take(4 * n1);
+    tb.hist = (uint32_t*)take(4 * (size_t)rsi::kSortBins * (tb.ntiles > 0 ? tb.ntiles : 1));
+    tb.partial = (float*)take(4 * 6 * (size_t)(nblk > 0 ? nblk : 1));
+    tb.bounds = (float*)take(4 * 6 * (size_t)M);
+    tb.child = (int32_t*)take(4 * 2 * n1);
+    tb.range = (int32_t*)take(4 * 2 * n1);
+    tb.parent = (int32_t*)take(4 * 2 * n1);
+    tb.flag = (int32_t*)take(4 * n1);
+    tb.nbox = (float4*)take(16 * 2 * n1);
+    tb.lbox = (float4*)take(16 * 2 * n1);
+    tb.nodes = (float4*)take(16 * 4 * n1);
+    tb.tris = (float4*)take(16 * 3 * n1);
+    tb.treelet = (float4*)take(M == 1 ? 16 * 4 * (size_t)rsi::kTreeletMax : 16);
+    tb.treelet_n = (int32_t*)take(4);
+    tb.status = (int32_t*)take(4);
+    return off;
+}
+
+rsi_status check_build_opts(const rsi_build_opts* o, int32_t* leaf, int32_t* levels) {
+    *leaf = 1;
+    *levels = 10;
+    if (!o) return RSI_OK;
+    if (o->leaf_size < 0 || o->leaf_size > rsi::kMaxLeaf) return RSI_ERR_ARG;
+    if (o->top_levels < -1 || o->top_levels > 12) return RSI_ERR_ARG;
+    if (o->leaf_size > 0) *leaf = o->leaf_size;
+    if (o->top_levels == -1)
+        *levels = 0;
+    else if (o->top_levels > 0)
+        *levels = o->top_levels;
+    return RSI_OK;
+}
+
+struct LaunchCfg {
+    int block, stack, smem_nodes;
+    bool stats;
+};
+
+rsi_status check_launch_opts(const rsi_launch_opts* lo, bool has_treelet, LaunchCfg* c) {
+    c->block = 256;
+    c->stack = 64;
+    c->smem_nodes = 0;
+    c->stats = false;
+    int sm = 0;
+    if (lo) {
+        if (lo->block_size != 0) {
+            if (lo->block_size < 32 || lo->block_size > 1024 || lo->block_size % 32) return RSI_ERR_ARG;
+            c->block = lo->block_size;
+        }
+        if (lo->stack_depth != 0) {
+            if (lo->stack_depth != 16 && lo->stack_depth != 32 && lo->stack_depth != 64)
+                return RSI_ERR_ARG;
+            c->stack = lo->stack_depth;
+        }
+        if (lo->smem_nodes < -1 || lo->smem_nodes > rsi::kTreeletMax) return RSI_ERR_ARG;
+        sm = lo->smem_nodes;
+        c->stats = lo->stats != 0;
+    }
+    if (has_treelet && sm != -1) c->smem_nodes = sm == 0 ? kDefaultSmemNodes : sm;
+    return RSI_OK;
+}
+
+rsi_status check_output(rsi_mode mode, const rsi_output* out) {
+    if (!out) return RSI_ERR_ARG;
+    if (mode == RSI_MODE_BOOL && !out->flag) return RSI_ERR_ARG;
+    if (mode == RSI_MODE_COUNT && !out->count) return RSI_ERR_ARG;
+    if (mode == RSI_MODE_NEAREST && !out->tri) return RSI_ERR_ARG;
+    if (mode != RSI_MODE_BOOL && out->hit_idx && (!out->n_hits || out->hit_cap < 0))
+        return RSI_ERR_ARG;
+    return RSI_OK;
+}
+
+rsi::TravOut trav_out(rsi_mode mode, const rsi_output* o) {
+    rsi::TravOut t;
+    memset(&t, 0, sizeof(t));
+    t.flag = o->flag;
+    t.count = o->count;
+    t.tri = o->tri;
+    t.tuv = o->tuv;
+    t.point = o->point;
+    t.dist = o->dist;
+    if (mode != RSI_MODE_BOOL && o->hit_idx) {
+        t.hit_idx = o->hit_idx;
+        t.hit_cap = o->hit_cap;
+        t.n_hits = o->n_hits;
+        t.hit_tri = o->hit_tri;
+        t.hit_dist = o->hit_dist;
+        t.hit_point = o->hit_point;
+        t.hit_count = o->hit_count;
+    }
+    return t;
+}
+
+}  // namespace
+
+struct rsi_bvh_s {
+    int device = 0;
+    int64_t nV = 0, nT = 0;
+    int32_t leaf = 1, levels = 10;
+    TreeBufs tb;
+    char* mem = nullptr;
+    size_t bytes = 0;
+    unsigned long long* scratch = nullptr;  // [0] work counter, [1..6] stats
+    bool built = false;
+    cudaStream_t stream = nullptr;
+};
+
+extern "C" {
+
+const char* rsi_version(void) { return "librsi 1.0 (sm_103a)"; }
+
+const char* rsi_status_string(rsi_status s) {
+    switch (s) {
+        case RSI_OK: return "ok";
+        case RSI_ERR_ARG: return "invalid argument";
+        case RSI_ERR_CUDA: return "CUDA runtime error";
+        case RSI_ERR_OOM: return "device out of memory";
+        case RSI_ERR_BAD_INDEX: return "triangle index out of range";
+        case RSI_ERR_STACK_OVERFLOW: return "traversal stack overflow";
+        case RSI_ERR_TIMEOUT: return "device-side wait timed out";
+        case RSI_ERR_NOT_BUILT: return "tree not built";
+    }
+    return "unknown status";
+}
+
+rsi_status rsi_bvh_create(int64_t nV, int64_t nT, const rsi_build_opts* opt, rsi_stream s,
+                          rsi_bvh* out) {
+    if (!out) return RSI_ERR_ARG;
+    *out = nullptr;
+    if (nV < 0 || nT < 0 || nT >= (int64_t)1 << 31) return RSI_ERR_ARG;
+    int32_t leaf, levels;
+    rsi_status st = check_build_opts(opt, &leaf, &levels);
+    if (st != RSI_OK) return st;
+    rsi_bvh h = new rsi_bvh_s();
+    RSI_CK(cudaGetDevice(&h->device));
+    h->nV = nV;
+    h->nT = nT;
+    h->leaf = leaf;
+    h->levels = levels;
+    const int nblk = (int)((nT + rsi::kBuildChunk - 1) / rsi::kBuildChunk);
+    TreeBufs tb;
+    memset(&tb, 0, sizeof(tb));
+    size_t bytes = carve(tb, nT, 1, nblk, nullptr) + 256;
+    cudaStream_t cs = (cudaStream_t)s;
+    cudaError_t e = cudaMallocAsync((void**)&h->mem, bytes, cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return e == cudaErrorMemoryAllocation ? RSI_ERR_OOM : RSI_ERR_CUDA;
+    }
+    carve(tb, nT, 1, nblk, h->mem);
+    h->scratch = (unsigned long long*)(h->mem + bytes - 256);
+    tb.leaf_size = leaf;
+    tb.top_levels = levels;
+    tb.sorted = 0;
+    h->tb = tb;
+    h->bytes = bytes;
+    h->stream = cs;
+    e = cudaMemsetAsync(tb.status, 0, 4, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tb.treelet_n, 0, 4, cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(h->mem, cs);
+        delete h;
+        return RSI_ERR_CUDA;
+    }
+    *out = h;
+    return RSI_OK;
+}
+
+rsi_status rsi_bvh_build(rsi_bvh h, const float* dV, const int32_t* dT, rsi_stream s) {
+    if (!h) return RSI_ERR_ARG;
+    if (h->nT > 0 && (!dV || !dT)) return RSI_ERR_ARG;
+    MeshArgs ma;
+    memset(&ma, 0, sizeof(ma));
+    ma.M = 1;
+    ma.one.V = dV;
+    ma.one.T = dT;
+    ma.one.nV = h->nV;
+    ma.one.n = (int32_t)h->nT;
+    ma.one.off = 0;
+    ma.one.blk0 = 0;
+    ma.one.nblk = h->tb.nblk;
+    h->tb.leaf_size = h->leaf;
+    h->tb.top_levels = h->levels;
+    RSI_CK(rsi::build_tree(h->tb, ma, (cudaStream_t)s, false));
+    h->built = true;
+    h->stream = (cudaStream_t)s;
+    return RSI_OK;
+}
+
+rsi_status rsi_build_bvh(const float* dV, int64_t nV, const int32_t* dT, int64_t nT,
+                         const rsi_build_opts* opt, rsi_stream s, rsi_bvh* out) {
+    rsi_status st = rsi_bvh_create(nV, nT, opt, s, out);
+    if (st != RSI_OK) return st;
+    st = rsi_bvh_build(*out, dV, dT, s);
+    if (st != RSI_OK) {
+        rsi_bvh_destroy(*out);
+        *out = nullptr;
+    }
+    return st;
+}
+
+rsi_status rsi_refit(rsi_bvh h, const float* dV, const int32_t* dT, rsi_stream s) {
+    if (!h || (h->nT > 0 && (!dV || !dT))) return RSI_ERR_ARG;
+    if (!h->built) return RSI_ERR_NOT_BUILT;
+    MeshArgs ma;
+    memset(&ma, 0, sizeof(ma));
+    ma.M = 1;
+    ma.one.V = dV;
+    ma.one.T = dT;
+    ma.one.nV = h->nV;
+    ma.one.n = (int32_t)h->nT;
+    ma.one.nblk = h->tb.nblk;
+    RSI_CK(rsi::build_tree(h->tb, ma, (cudaStream_t)s, true));
+    h->stream = (cudaStream_t)s;
+    return RSI_OK;
+}
+
+rsi_status rsi_bvh_status(rsi_bvh h, rsi_stream s) {
+    if (!h) return RSI_ERR_ARG;
+    int32_t v = 0;
+    RSI_CK(cudaMemcpyAsync(&v, h->tb.status, 4, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+    RSI_CK(cudaStreamSynchronize((cudaStream_t)s));
+    RSI_CK(cudaMemsetAsync(h->tb.status, 0, 4, (cudaStream_t)s));
+    RSI_CK(cudaStreamSynchronize((cudaStream_t)s));
+    return (rsi_status)v;
+}
+
+rsi_status rsi_bvh_get_info(rsi_bvh h, rsi_bvh_info* info) {
+    if (!h || !info) return RSI_ERR_ARG;
+    info->n_vertices = h->nV;
+    info->n_triangles = h->nT;
+    info->leaf_size = h->leaf;
+    int32_t tn = 0;
+    if (h->built && h->levels > 0) {
+        RSI_CK(cudaStreamSynchronize(h->stream));
+        RSI_CK(cudaMemcpy(&tn, h->tb.treelet_n, 4, cudaMemcpyDeviceToHost));
+    }
+    info->treelet_nodes = tn;
+    info->device_bytes = (int64_t)h->bytes;
+    return RSI_OK;
+}
+
+rsi_status rsi_bvh_destroy(rsi_bvh h) {
+    if (!h) return RSI_ERR_ARG;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != h->device) cudaSetDevice(h->device);
+    cudaError_t e = cudaFreeAsync(h->mem, h->stream);
+    if (cur != h->device) cudaSetDevice(cur);
+    delete h;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return RSI_ERR_CUDA;
+    }
+    return RSI_OK;
+}
+
+rsi_status rsi_bvh_export(rsi_bvh h, rsi_stream s, float* bounds, uint32_t* codes, int32_t* order,
+                          int32_t* left, int32_t* right, int32_t* range, float* nbox, float* lbox,
+                          float* nodes) {
+    if (!h) return RSI_ERR_ARG;
+    if (!h->built) return RSI_ERR_NOT_BUILT;
+    RSI_CK(cudaStreamSynchronize((cudaStream_t)s));
+    RSI_CK(cudaStreamSynchronize(h->stream));
+    const int64_t N = h->nT;
+    const TreeBufs& tb = h->tb;
+    if (bounds) RSI_CK(cudaMemcpy(bounds, tb.bounds, 24, cudaMemcpyDeviceToHost));
+    if (N == 0) return RSI_OK;
+    if (codes) {
+        std::vector<uint64_t> k(N);
+        RSI_CK(cudaMemcpy(k.data(), tb.keys[tb.sorted], 8 * N, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < N; ++i) codes[i] = (uint32_t)k[i];
+    }
+    if (order) RSI_CK(cudaMemcpy(order, tb.vals[tb.sorted], 4 * N, cudaMemcpyDeviceToHost));
+    if (left || right || range) {
+        std::vector<int32_t> c(2 * N), r(2 * N);
+        RSI_CK(cudaMemcpy(c.data(), tb.child, 8 * N, cudaMemcpyDeviceToHost));
+        RSI_CK(cudaMemcpy(r.data(), tb.range, 8 * N, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i + 1 < N; ++i) {
+            if (left) left[i] = c[2 * i];
+            if (right) right[i] = c[2 * i + 1];
+            if (range) {
+                range[2 * i] = r[2 * i];
+                range[2 * i + 1] = r[2 * i + 1];
+            }
+        }
+    }
+    auto boxes = [&](const float4* src, int64_t n, float* dst) -> rsi_status {
+        std::vector<float4> b(2 * (n > 0 ? n : 1));
+        if (n > 0) RSI_CK(cudaMemcpy(b.data(), src, 32 * n, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n; ++i) {
+            dst[6 * i + 0] = b[2 * i].x;
+            dst[6 * i + 1] = b[2 * i].y;
+            dst[6 * i + 2] = b[2 * i].z;
+            dst[6 * i + 3] = b[2 * i + 1].x;
+            dst[6 * i + 4] = b[2 * i + 1].y;
+            dst[6 * i + 5] = b[2 * i + 1].z;
+        }
+        return RSI_OK;
+    };
+    if (nbox) {
+        rsi_status st = boxes(tb.nbox, N - 1, nbox);
+        if (st != RSI_OK) return st;
+    }
+    if (lbox) {
+        rsi_status st = boxes(tb.lbox, N, lbox);
+        if (st != RSI_OK) return st;
+    }
+    if (nodes) RSI_CK(cudaMemcpy(nodes, tb.nodes, 64 * N, cudaMemcpyDeviceToHost));
+    return RSI_OK;
+}
+
+static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, int64_t nR,
+                                 rsi_mode mode, const rsi_output* out, const rsi_launch_opts* lo,
+                                 rsi_stream s, bool force_stats) {
+    if (!h || nR < 0) return RSI_ERR_ARG;
+    if (mode != RSI_MODE_BOOL && mode != RSI_MODE_COUNT && mode != RSI_MODE_NEAREST)
+        return RSI_ERR_ARG;
+    rsi_status st = check_output(mode, out);
+    if (st != RSI_OK) return st;
+    if (!h->built) return RSI_ERR_NOT_BUILT;
+    LaunchCfg c;
+    st = check_launch_opts(lo, h->levels > 0 && h->nT > 0, &c);
+    if (st != RSI_OK) return st;
+    if (force_stats) c.stats = true;
+    if (nR == 0) {
+        if (mode != RSI_MODE_BOOL && out->hit_idx)
+            RSI_CK(cudaMemsetAsync(out->n_hits, 0, 8, (cudaStream_t)s));
+        return RSI_OK;
+    }
+    if (!dA || !dB) return RSI_ERR_ARG;
+    rsi::TraceParams P;
+    memset(&P, 0, sizeof(P));
+    P.A = dA;
+    P.B = dB;
+    P.nR = nR;
+    if (h->nT == 0)
+        P.root = rsi::kNoRoot;
+    else if (h->levels > 0)
+        P.root = ~0;
+    else
+        P.root = (int)(h->nT - 1);
+    P.nodes = h->tb.nodes;
+    P.tris = h->tb.tris;
+    P.treelet = h->tb.treelet;
+    P.treelet_n = h->tb.treelet_n;
+    P.smem_nodes = c.smem_nodes;
+    P.work = h->scratch;
+    P.stats = h->scratch + 1;
+    P.out = trav_out(mode, out);
+    if (c.stats) RSI_CK(cudaMemsetAsync(P.stats, 0, 6 * 8, (cudaStream_t)s));
+    RSI_CK(rsi::launch_trace(P, mode, c.stack, c.stats, c.block, (cudaStream_t)s));
+    return RSI_OK;
+}
+
+rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR, rsi_mode mode,
+                         const rsi_output* out, const rsi_launch_opts* lo, rsi_stream s) {
+    return intersect_impl(h, dA, dB, nR, mode, out, lo, s, false);
+}
+
+rsi_status rsi_intersect_stats(rsi_bvh h, const float* dA, const float* dB, int64_t nR,
+                               rsi_mode mode, const rsi_output* out, const rsi_launch_opts* lo,
+                               rsi_stream s, rsi_stats* stt) {
+    if (!stt) return RSI_ERR_ARG;
+    memset(stt, 0, sizeof(*stt));
+    rsi_status st = intersect_impl(h, dA, dB, nR, mode, out, lo, s, true);
+    if (st != RSI_OK || nR == 0) return st;
+    unsigned long long v[6];
+    RSI_CK(cudaMemcpyAsync(v, h->scratch + 1, 48, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+    RSI_CK(cudaStreamSynchronize((cudaStream_t)s));
+    stt->segments = (int64_t)v[0];
+    stt->node_visits = (int64_t)v[1];
+    stt->tri_tests = (int64_t)v[2];
+    stt->fp64_tests = (int64_t)v[3];
+    stt->fp64_refines = (int64_t)v[4];
+    stt->overflows = (int64_t)v[5];
+    return RSI_OK;
+}
+
+rsi_status rsi_intersect_backward(const float* dV, int64_t nV, const int32_t* dT, int64_t nT,
+                                  const float* dA, const float* dB, int64_t nR,
+                                  const int32_t* dTri, const float* dTuv, const float* dGradPoint,
+                                  const float* dGradTuv, float* dGradV, float* dGradA,
+                                  float* dGradB, rsi_stream s) {
+    if (nV < 0 || nT < 0 || nR < 0) return RSI_ERR_ARG;
+    if (nR == 0) return RSI_OK;
+    if (!dA || !dB || !dTri || !dTuv || (nT > 0 && (!dV || !dT))) return RSI_ERR_ARG;
+    RSI_CK(rsi::launch_backward(dV, nV, dT, nT, dA, dB, nR, dTri, dTuv, dGradPoint, dGradTuv,
+                                dGradV, dGradA, dGradB, (cudaStream_t)s));
+    return RSI_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batch
+struct rsi_batch_s {
+    int device = 0;
+    std::vector<rsi_batch_item> items;
+    TreeBufs tb;
+    char* mem = nullptr;
+    size_t bytes = 0;
+    MeshDesc* d_table = nullptr;
+    int32_t* d_blkmesh = nullptr;
+    rsi::BatchItemDev* d_items = nullptr;
+    unsigned long long* work = nullptr;
+    int64_t n_chunks = 0;
+    LaunchCfg cfg;
+    int32_t leaf = 1;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t g_full = nullptr, g_trav = nullptr;
+    cudaStream_t stream = nullptr;
+};
+
+extern "C" {
+
+rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_build_opts* bo,
+                            const rsi_launch_opts* lo, rsi_stream s, rsi_batch* out) {
+    if (!out || n < 1 || !items) return RSI_ERR_ARG;
+    *out = nullptr;
+    int32_t leaf, levels;
+    rsi_status st = check_build_opts(bo, &leaf, &levels);
+    if (st != RSI_OK) return st;
+    LaunchCfg cfg;
+    st = check_launch_opts(lo, false, &cfg);
+    if (st != RSI_OK) return st;
+    int64_t N = 0;
+    int nblk = 0;
+    std::vector<MeshDesc> table(n);
+    std::vector<int32_t> blkmesh;
+    for (int k = 0; k < n; ++k) {
+        const rsi_batch_item& it = items[k];
+        if (it.nV < 0 || it.nT < 0 || it.nR < 0) return RSI_ERR_ARG;
+        if (it.nT > 0 && (!it.dV || !it.dT)) return RSI_ERR_ARG;
+        if (it.nR > 0 && (!it.dA || !it.dB)) return RSI_ERR_ARG;
+        if (it.mode < 0 || it.mode > 2) return RSI_ERR_ARG;
+        st = check_output((rsi_mode)it.mode, &it.out);
+        if (st != RSI_OK) return st;
+        MeshDesc& md = table[k];
+        md.V = it.dV;
+        md.T = it.dT;
+        md.nV = it.nV;
+        md.n = (int32_t)it.nT;
+        md.off = (int32_t)N;
+        md.blk0 = nblk;
+        md.nblk = (int32_t)((it.nT + rsi::kBuildChunk - 1) / rsi::kBuildChunk);
+        for (int q = 0; q < md.nblk; ++q) blkmesh.push_back(k);
+        nblk += md.nblk;
+        N += it.nT;
+        if (N >= ((int64_t)1 << 31)) return RSI_ERR_ARG;
+    }
+    // work order: items by decreasing estimated cost per segment
+    std::vector<int> ord(n);
+    for (int k = 0; k < n; ++k) ord[k] = k;
+    auto cost = [&](int k) {
+        const double w = items[k].mode == RSI_MODE_BOOL ? 1.0 : 1.5;
+        return w * std::log2(2.0 + (double)items[k].nT);
+    };
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::vector<rsi::BatchItemDev> dev(n);
+    int64_t chunk = 0;
+    for (int q = 0; q < n; ++q) {
+        const int k = ord[q];
+        const rsi_batch_item& it = items[k];
+        rsi::BatchItemDev& d = dev[q];
+        d.A = it.dA;
+        d.B = it.dB;
+        d.nR = it.nR;
+        d.root = it.nT > 0 ? (int)(table[k].off + it.nT - 1) : rsi::kNoRoot;
+        d.mode = it.mode;
+        d.chunk0 = chunk;
+        d.out = trav_out((rsi_mode)it.mode, &it.out);
+        chunk += (it.nR + 31) / 32;
+    }
+    rsi_batch b = new rsi_batch_s();
+    RSI_CK(cudaGetDevice(&b->device));
+    b->items.assign(items, items + n);
+    b->cfg = cfg;
+    b->leaf = leaf;
+    b->n_chunks = chunk;
+    TreeBufs tb;
+    memset(&tb, 0, sizeof(tb));
+    const size_t tree_bytes = carve(tb, N, n, nblk, nullptr);
+    const size_t tab_bytes = align256(sizeof(MeshDesc) * n);
+    const size_t blk_bytes = align256(sizeof(int32_t) * (blkmesh.size() + 1));
+    const size_t item_bytes = align256(sizeof(rsi::BatchItemDev) * n);
+    const size_t bytes = tree_bytes + tab_bytes + blk_bytes + item_bytes + 256;
+    cudaStream_t cs = (cudaStream_t)s;
+    cudaError_t e = cudaMallocAsync((void**)&b->mem, bytes, cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return e == cudaErrorMemoryAllocation ? RSI_ERR_OOM : RSI_ERR_CUDA;
+    }
+    carve(tb, N, n, nblk, b->mem);
+    tb.leaf_size = leaf;
+    tb.top_levels = 0;
+    b->tb = tb;
+    b->bytes = bytes;
+    b->d_table = (MeshDesc*)(b->mem + tree_bytes);
+    b->d_blkmesh = (int32_t*)(b->mem + tree_bytes + tab_bytes);
+    b->d_items = (rsi::BatchItemDev*)(b->mem + tree_bytes + tab_bytes + blk_bytes);
+    b->work = (unsigned long long*)(b->mem + bytes - 256);
+    b->stream = cs;
+    e = cudaMemcpyAsync(b->d_table, table.data(), sizeof(MeshDesc) * n, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && !blkmesh.empty())
+        e = cudaMemcpyAsync(b->d_blkmesh, blkmesh.data(), sizeof(int32_t) * blkmesh.size(),
+                            cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_items, dev.data(), sizeof(rsi::BatchItemDev) * n,
+                            cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tb.status, 0, 4, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);  // host tables go out of scope
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(b->mem, cs);
+        delete b;
+        return RSI_ERR_CUDA;
+    }
+    *out = b;
+    return RSI_OK;
+}
+
+static MeshArgs batch_mesh_args(rsi_batch b) {
+    MeshArgs ma;
+    memset(&ma, 0, sizeof(ma));
+    ma.M = b->tb.M;
+    ma.table = b->d_table;
+    ma.blk_mesh = b->d_blkmesh;
+    if (ma.M == 1) {
+        const rsi_batch_item& it = b->items[0];
+        ma.one.V = it.dV;
+        ma.one.T = it.dT;
+        ma.one.nV = it.nV;
+        ma.one.n = (int32_t)it.nT;
+        ma.one.nblk = b->tb.nblk;
+    }
+    return ma;
+}
+
+rsi_status rsi_batch_build(rsi_batch b, rsi_stream s) {
+    if (!b) return RSI_ERR_ARG;
+    RSI_CK(rsi::build_tree(b->tb, batch_mesh_args(b), (cudaStream_t)s, false));
+    return RSI_OK;
+}
+
+rsi_status rsi_batch_intersect(rsi_batch b, rsi_stream s) {
+    if (!b) return RSI_ERR_ARG;
+    rsi::BatchParams P;
+    P.items = b->d_items;
+    P.n_items = (int)b->items.size();
+    P.n_chunks = b->n_chunks;
+    P.nodes = b->tb.nodes;
+    P.tris = b->tb.tris;
+    P.work = b->work;
+    RSI_CK(rsi::launch_batch(P, b->cfg.block, b->cfg.stack, (cudaStream_t)s));
+    return RSI_OK;
+}
+
+rsi_status rsi_batch_run_graph(rsi_batch b, int32_t rebuild, rsi_stream s) {
+    if (!b) return RSI_ERR_ARG;
+    cudaGraphExec_t* slot = rebuild ? &b->g_full : &b->g_trav;
+    if (!*slot) {
+        cudaGraph_t g = nullptr;
+        RSI_CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        rsi_status st = RSI_OK;
+        if (rebuild) st = rsi_batch_build(b, (rsi_stream)b->cap);
+        if (st == RSI_OK) st = rsi_batch_intersect(b, (rsi_stream)b->cap);
+        cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+        if (st != RSI_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        RSI_CK(e);
+        e = cudaGraphInstantiate(slot, g, 0);
+        cudaGraphDestroy(g);
+        RSI_CK(e);
+    }
+    RSI_CK(cudaGraphLaunch(*slot, (cudaStream_t)s));
+    return RSI_OK;
+}
+
+rsi_status rsi_batch_destroy(rsi_batch b) {
+    if (!b) return RSI_ERR_ARG;
+    if (b->g_full) cudaGraphExecDestroy(b->g_full);
+    if (b->g_trav) cudaGraphExecDestroy(b->g_trav);
+    cudaStreamSynchronize(b->stream);
+    cudaError_t e = cudaFreeAsync(b->mem, b->stream);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return RSI_ERR_CUDA;
+    }
+    return RSI_OK;
+}
+
+// ------------------------------------------------------------------ tuner
+rsi_status rsi_autotune(rsi_bvh h, const float* dV, const int32_t* dT, const float* dA,
+                        const float* dB, int64_t nR, rsi_mode mode, const rsi_output* out,
+                        const int32_t* block_sizes, int32_t n_bs, const int32_t* stack_depths,
+                        int32_t n_sd, const int32_t* smem_nodes, int32_t n_sm,
+                        const int32_t* leaf_sizes, int32_t n_ls, int32_t reps, rsi_stream s,
+                        rsi_tune_entry* table, int32_t cap, int32_t* n_written,
+                        rsi_launch_opts* best_lo, int32_t* best_leaf) {
+    if (!h || !block_sizes || !stack_depths || !smem_nodes || !leaf_sizes || n_bs < 1 ||
+        n_sd < 1 || n_sm < 1 || n_ls < 1 || reps < 1 || !best_lo || !best_leaf || nR <= 0)
+        return RSI_ERR_ARG;
+    cudaStream_t cs = (cudaStream_t)s;
+    cudaEvent_t e0, e1;
+    RSI_CK(cudaEventCreate(&e0));
+    RSI_CK(cudaEventCreate(&e1));
+    float best_ms = INFINITY;
+    int32_t written = 0;
+    const int32_t leaf0 = h->leaf;
+    *best_leaf = leaf0;
+    memset(best_lo, 0, sizeof(*best_lo));
+    rsi_status result = RSI_OK;
+    for (int li = 0; li < n_ls && result == RSI_OK; ++li) {
+        if (leaf_sizes[li] < 1 || leaf_sizes[li] > rsi::kMaxLeaf) {
+            result = RSI_ERR_ARG;
+            break;
+        }
+        h->leaf = leaf_sizes[li];
+        result = rsi_bvh_build(h, dV, dT, s);
+        if (result != RSI_OK) break;
+        for (int bi = 0; bi < n_bs && result == RSI_OK; ++bi)
+            for (int si = 0; si < n_sd && result == RSI_OK; ++si)
+                for (int mi = 0; mi < n_sm && result == RSI_OK; ++mi) {
+                    rsi_launch_opts lo;
+                    memset(&lo, 0, sizeof(lo));
+                    lo.block_size = block_sizes[bi];
+                    lo.stack_depth = stack_depths[si];
+                    lo.smem_nodes = smem_nodes[mi];
+                    result = rsi_intersect(h, dA, dB, nR, mode, out, &lo, s);  // warm-up
+                    if (result != RSI_OK) break;
+                    std::vector<float> ms(reps);
+                    for (int r = 0; r < reps && result == RSI_OK; ++r) {
+                        cudaEventRecord(e0, cs);
+                        result = rsi_intersect(h, dA, dB, nR, mode, out, &lo, s);
+                        cudaEventRecord(e1, cs);
+                        if (cudaEventSynchronize(e1) != cudaSuccess) result = RSI_ERR_CUDA;
+                        cudaEventElapsedTime(&ms[r], e0, e1);
+                    }
+                    if (result != RSI_OK) break;
+                    std::sort(ms.begin(), ms.end());
+                    const float med = ms[reps / 2];
+                    if (table && written < cap) {
+                        rsi_tune_entry& t = table[written];
+                        t.block_size = lo.block_size;
+                        t.stack_depth = lo.stack_depth;
+                        t.smem_nodes = lo.smem_nodes;
+                        t.leaf_size = h->leaf;
+                        t.ms = med;
+                    }
+                    ++written;
+                    if (med < best_ms) {
+                        best_ms = med;
+                        *best_lo = lo;
+                        *best_leaf = h->leaf;
+                    }
+                }
+    }
+    if (n_written) *n_written = written < cap ? written : cap;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->leaf = result == RSI_OK ? *best_leaf : leaf0;
+    rsi_status rb = rsi_bvh_build(h, dV, dT, s);
+    if (result == RSI_OK) result = rb;
+    if (result == RSI_OK) RSI_CK(cudaStreamSynchronize(cs));
+    return result;
+}
+
+}  // extern "C"

@@ -1,0 +1,17 @@
+// Host-side entry points shared between the translation units of librsi.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rsi_internal.cuh"
+
+namespace rsi {
+
+// Enqueue the LBVH build (or, with refit, only the bottom-up box pass and the
+// treelet) of the meshes described by `ma` into the buffers of `tb` on s.
+cudaError_t build_tree(TreeBufs& tb, const MeshArgs& ma, cudaStream_t s, bool refit);
+
+// Number of kernel launches build_tree enqueues.
+int build_launches(const TreeBufs& tb, bool refit);
+
+}  // namespace rsi

@@ -1,0 +1,287 @@
+// Internal declarations of librsi (not part of the public ABI).
+//
+// Data layout in device memory (one mesh of n triangles at offset `off` in
+// the concatenated arrays; a batch concatenates its meshes):
+//   keys[2]/vals[2]  u64 sort keys (mesh << 32 | Morton code) / u32 global
+//                    triangle index, ping-pong buffers of the radix sort
+//   child[2N]        Karras children of internal slot g: >= 0 internal slot,
+//                    < 0 leaf -(global sorted position + 1)
+//   range[2N]        first, last leaf (global sorted positions) of slot g
+//   parent[2N]       [0,N): parent of internal slot, [N,2N): parent of leaf
+//   nbox/lbox[2N]    float4 lo, hi boxes of internal slots / leaves
+//   nodes[4N]        traversal node per slot = 4 x float4 = 64 B:
+//                      {c0.lo.x, c0.lo.y, c0.lo.z, c0.hi.x}
+//                      {c0.hi.y, c0.hi.z, c1.lo.x, c1.lo.y}
+//                      {c1.lo.z, c1.hi.x, c1.hi.y, c1.hi.z}
+//                      {ref0, ref1, cnt0, cnt1} as int bit patterns
+//                    cnt > 0: leaf of cnt triangles starting at sorted
+//                    position ref; cnt == 0: internal slot ref; cnt == -1:
+//                    treelet node ref (only inside the treelet copy).
+//                    Slot off+n-1 is the root slot (the paper keeps its root
+//                    pointer in internalNodes[N_t-1] the same way, Sec. 3.1):
+//                    child0 = the Karras root, child1 = empty.
+//   tris[3N]         triangles in leaf order: {v0, orig id}, {v1, -}, {v2, -}
+//   treelet[4 S]     breadth-first copy of the top of one mesh's tree
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rsi.h"
+
+namespace rsi {
+
+constexpr int kMaxLeaf = 8;
+constexpr int kTreeletMax = 2048;   // nodes in the breadth-first top treelet
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile
+constexpr int kSortBins = 256;
+constexpr int kBuildThreads = 256;
+constexpr int kBuildChunk = 2048;   // triangles per block in bounds / Morton
+
+// FP32 filter constants (see mt32 below).
+constexpr float kFilterK = 0x1p-17f;
+constexpr float kFilterEta = 0x1p-100f;
+constexpr float kRangeLo = 0x1p-30f;
+constexpr float kRangeHi = 0x1p30f;
+constexpr float kSlabSlack = 0x1p-18f;
+constexpr float kTinyDir = 0x1p-60f;
+
+struct MeshDesc {
+    const float* V;
+    const int32_t* T;
+    int64_t nV;
+    int32_t n;     // triangles
+    int32_t off;   // offset in concatenated triangle / node arrays
+    int32_t blk0;  // first block of this mesh in the bounds / Morton grid
+    int32_t nblk;
+};
+
+struct MeshArgs {
+    int32_t M;                // number of meshes
+    const MeshDesc* table;    // device table (M > 1)
+    const int32_t* blk_mesh;  // block -> mesh (M > 1)
+    MeshDesc one;             // inline descriptor (M == 1)
+};
+
+__device__ __forceinline__ MeshDesc mesh_of(const MeshArgs& a, int m) {
+    return a.M == 1 ? a.one : a.table[m];
+}
+
+struct TreeBufs {
+    int32_t N;  // total triangles
+    int32_t M;  // meshes
+    uint64_t* keys[2];
+    uint32_t* vals[2];
+    uint32_t* hist;
+    int32_t ntiles;
+    int32_t nblk;     // blocks of the bounds / Morton grid
+    float* partial;   // 6 * nblk
+    float* bounds;    // 6 * M
+    int32_t* child;   // 2N
+    int32_t* range;   // 2N
+    int32_t* parent;  // 2N
+    int32_t* flag;    // N
+    float4* nbox;     // 2N
+    float4* lbox;     // 2N
+    float4* nodes;    // 4N
+    float4* tris;     // 3N
+    float4* treelet;  // 4 * kTreeletMax (single-mesh trees)
+    int32_t* treelet_n;
+    int32_t* status;  // device status word (rsi_status)
+    int32_t leaf_size;
+    int32_t top_levels;  // < 0: no treelet
+    int32_t sorted;      // which keys/vals buffer holds the sorted result
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ float4 ld4(const float4* p) { return __ldg(p); }
+
+__device__ __forceinline__ int f2i(float x) { return __float_as_int(x); }
+__device__ __forceinline__ float i2f(int x) { return __int_as_float(x); }
+
+__device__ __forceinline__ float maxabs3(float x, float y, float z) {
+    return fmaxf(fmaxf(fabsf(x), fabsf(y)), fabsf(z));
+}
+
+__device__ __forceinline__ bool finite3(float x, float y, float z) {
+    return isfinite(x) && isfinite(y) && isfinite(z);
+}
+
+// Per-segment registers of the traversal.
+struct Seg {
+    float ax, ay, az;  // start a
+    float dx, dy, dz;  // d = fl(b - a)
+    float ix, iy, iz;  // 1 / d (IEEE; +-inf for a zero component)
+    float md;          // max |d_i|
+    bool tiny;         // some 0 < |d_i| < 2^-60: boxes tested by overlap instead
+    bool fp64only;     // |d| outside the FP32 filter's range: decide in FP64
+};
+
+__device__ __forceinline__ bool seg_setup(const float* A, const float* B, int64_t i, Seg& s) {
+    const float ax = A[3 * i], ay = A[3 * i + 1], az = A[3 * i + 2];
+    const float bx = B[3 * i], by = B[3 * i + 1], bz = B[3 * i + 2];
+    if (!(finite3(ax, ay, az) && finite3(bx, by, bz))) return false;
+    s.ax = ax; s.ay = ay; s.az = az;
+    s.dx = __fsub_rn(bx, ax);
+    s.dy = __fsub_rn(by, ay);
+    s.dz = __fsub_rn(bz, az);
+    // An overflowing difference (|b - a| > FLT_MAX) gives 1/d = 0: that axis
+    // then never culls (conservative) and every decision is taken in FP64.
+    s.ix = __frcp_rn(s.dx);
+    s.iy = __frcp_rn(s.dy);
+    s.iz = __frcp_rn(s.dz);
+    s.md = maxabs3(s.dx, s.dy, s.dz);
+    const float mn = fminf(fminf(s.dx != 0.f ? fabsf(s.dx) : 1.f, s.dy != 0.f ? fabsf(s.dy) : 1.f),
+                           s.dz != 0.f ? fabsf(s.dz) : 1.f);
+    s.tiny = mn < kTinyDir;
+    s.fp64only = !(s.md >= kRangeLo && s.md <= kRangeHi);
+    return true;
+}
+
+// Conservative segment / box test.  Per axis the entry parameter uses the
+// near face and the exit the far face (chosen by the sign of 1/d), computed
+// as (face - a) * (1/d): each has relative error <= 3u, so scaling the exit
+// by 1 + 2^-18 before `entry <= exit` never rejects a box the exact segment
+// a + s d, s in [0, tlim], touches.  A zero direction component gives
+// (face - a) * inf = +-inf (correct limit) or NaN when the segment lies in
+// the face plane; fmaxf / fminf drop NaN, which is the right answer there.
+__device__ __forceinline__ bool slab(const Seg& s, float lx, float ly, float lz, float hx,
+                                     float hy, float hz, float tlim, float& tent) {
+    if (s.tiny) {
+        // box-overlap test of the segment's own box; a + fl(b - a) is within
+        // 3u (|a| + |b|) of b, so the box is padded by 2^-21 (|a| + |a + d|)
+        tent = 0.f;
+        const float bx = s.ax + s.dx, by = s.ay + s.dy, bz = s.az + s.dz;
+        const float px = (fabsf(s.ax) + fabsf(bx)) * 0x1p-21f + 0x1p-140f;
+        const float py = (fabsf(s.ay) + fabsf(by)) * 0x1p-21f + 0x1p-140f;
+        const float pz = (fabsf(s.az) + fabsf(bz)) * 0x1p-21f + 0x1p-140f;
+        return !(fmaxf(s.ax, bx) + px < lx || fminf(s.ax, bx) - px > hx ||
+                 fmaxf(s.ay, by) + py < ly || fminf(s.ay, by) - py > hy ||
+                 fmaxf(s.az, bz) + pz < lz || fminf(s.az, bz) - pz > hz);
+    }
+    const bool nx = s.ix < 0.f, ny = s.iy < 0.f, nz = s.iz < 0.f;
+    const float tnx = (__fsub_rn(nx ? hx : lx, s.ax)) * s.ix;
+    const float tfx = (__fsub_rn(nx ? lx : hx, s.ax)) * s.ix;
+    const float tny = (__fsub_rn(ny ? hy : ly, s.ay)) * s.iy;
+    const float tfy = (__fsub_rn(ny ? ly : hy, s.ay)) * s.iy;
+    const float tnz = (__fsub_rn(nz ? hz : lz, s.az)) * s.iz;
+    const float tfz = (__fsub_rn(nz ? lz : hz, s.az)) * s.iz;
+    const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, 0.f));
+    const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tlim));
+    tent = tn;
+    return tn <= tf * (1.f + kSlabSlack);
+}
+
+// FP32 Moller-Trumbore with a static error filter.
+//
+// With u = 2^-24 and exact float inputs, each computed triple product
+// (det = e1.(d x e2), nU = s0.(d x e2), nV = d.(s0 x e1), nT = e2.(s0 x e1))
+// differs from its exact value by at most 6 gamma_8 m_a m_b m_c (< 48u M),
+// where m_x = max_i |x_i| of the three factors (FMA contraction only removes
+// roundings).  The two derived sums det - nU - nV and det - nT add <= 12u of
+// their magnitude.  A decision is certified when the value clears
+// K M + eta with K = 2^-17 (> 60u plus the FP64 definition's own error and
+// the rounding of M itself); eta covers underflow when every m lies in
+// [2^-30, 2^30] (else the FP64 path decides).  Certified decisions equal
+// those of the FP64 definition; the rest return 2 and are decided in FP64.
+// Returns 0 miss, 1 hit, 2 undecided.
+__device__ __forceinline__ int mt32(const Seg& s, const float4& A, const float4& B,
+                                    const float4& C, bool want, float& t, float& u, float& v,
+                                    float& err) {
+    const float e1x = B.x - A.x, e1y = B.y - A.y, e1z = B.z - A.z;
+    const float e2x = C.x - A.x, e2y = C.y - A.y, e2z = C.z - A.z;
+    const float m1 = maxabs3(e1x, e1y, e1z);
+    const float m2 = maxabs3(e2x, e2y, e2z);
+    // An exactly zero edge makes det exactly zero in FP64 too: never a hit.
+    if (m1 == 0.f || m2 == 0.f) return 0;
+    const float sx = s.ax - A.x, sy = s.ay - A.y, sz = s.az - A.z;
+    const float ms = maxabs3(sx, sy, sz);
+    const float px = s.dy * e2z - s.dz * e2y;
+    const float py = s.dz * e2x - s.dx * e2z;
+    const float pz = s.dx * e2y - s.dy * e2x;
+    const float det = e1x * px + e1y * py + e1z * pz;
+    const float qx = sy * e1z - sz * e1y;
+    const float qy = sz * e1x - sx * e1z;
+    const float qz = sx * e1y - sy * e1x;
+    float nu = sx * px + sy * py + sz * pz;
+    float nv = s.dx * qx + s.dy * qy + s.dz * qz;
+    float nt = e2x * qx + e2y * qy + e2z * qz;
+    const float mhi = fmaxf(fmaxf(m1, m2), ms);
+    const float mlo = fminf(fminf(m1, m2), ms == 0.f ? 1.f : ms);
+    if (s.fp64only || mhi > kRangeHi || mlo < kRangeLo) return 2;
+    const float Pde = s.md * m2, Pse = ms * m1;
+    const float Mdet = m1 * Pde, MU = ms * Pde, MV = s.md * Pse, MT = m2 * Pse;
+    const float Bdet = fmaf(kFilterK, Mdet, kFilterEta);
+    const float adet = fabsf(det);
+    if (!(adet > Bdet)) return 2;
+    if (det < 0.f) {
+        nu = -nu;
+        nv = -nv;
+        nt = -nt;
+    }
+    const float w = (adet - nu) - nv;
+    const float r = adet - nt;
+    const float BU = fmaf(kFilterK, MU, kFilterEta);
+    const float BV = fmaf(kFilterK, MV, kFilterEta);
+    const float BT = fmaf(kFilterK, MT, kFilterEta);
+    const float Bw = fmaf(kFilterK, Mdet + MU + MV, kFilterEta);
+    const float Br = fmaf(kFilterK, Mdet + MT, kFilterEta);
+    if (nu < -BU || nv < -BV || nt < -BT || w < -Bw || r < -Br) return 0;
+    if (!(nu > BU && nv > BV && nt > BT && w > Bw && r > Br)) return 2;
+    if (want) {
+        const float inv = __frcp_rn(adet);
+        t = nt * inv;
+        u = nu * inv;
+        v = nv * inv;
+        // |x_computed - x| <= (B_x + |x| B_det) / |det| + 4u |x|
+        const float eT = fmaf(t, Bdet, BT) * inv;
+        const float eU = fmaf(u, Bdet, BU) * inv;
+        const float eV = fmaf(v, Bdet, BV) * inv;
+        err = fmaxf(fmaxf(eT, eU), eV) * 1.0001f + 0x1p-21f;
+    }
+    return 1;
+}
+
+// The FP64 definition (public header) in its exact operation order: no
+// contraction, every product / sum rounded where written.  Inputs are the
+// float coordinates widened exactly.  Returns hit; t, u, v when hit.
+static __device__ __noinline__ int mt64(float ax_, float ay_, float az_, float bx_, float by_,
+                                 float bz_, float4 A, float4 B, float4 C, double* tuv) {
+    const double ax = ax_, ay = ay_, az = az_;
+    const double dx = __dsub_rn((double)bx_, ax), dy = __dsub_rn((double)by_, ay),
+                 dz = __dsub_rn((double)bz_, az);
+    const double v0x = A.x, v0y = A.y, v0z = A.z;
+    const double e1x = __dsub_rn((double)B.x, v0x), e1y = __dsub_rn((double)B.y, v0y),
+                 e1z = __dsub_rn((double)B.z, v0z);
+    const double e2x = __dsub_rn((double)C.x, v0x), e2y = __dsub_rn((double)C.y, v0y),
+                 e2z = __dsub_rn((double)C.z, v0z);
+    const double px = __dsub_rn(__dmul_rn(dy, e2z), __dmul_rn(dz, e2y));
+    const double py = __dsub_rn(__dmul_rn(dz, e2x), __dmul_rn(dx, e2z));
+    const double pz = __dsub_rn(__dmul_rn(dx, e2y), __dmul_rn(dy, e2x));
+    double det = __dadd_rn(__dadd_rn(__dmul_rn(e1x, px), __dmul_rn(e1y, py)), __dmul_rn(e1z, pz));
+    const double sx = __dsub_rn(ax, v0x), sy = __dsub_rn(ay, v0y), sz = __dsub_rn(az, v0z);
+    const double qx = __dsub_rn(__dmul_rn(sy, e1z), __dmul_rn(sz, e1y));
+    const double qy = __dsub_rn(__dmul_rn(sz, e1x), __dmul_rn(sx, e1z));
+    const double qz = __dsub_rn(__dmul_rn(sx, e1y), __dmul_rn(sy, e1x));
+    double nu = __dadd_rn(__dadd_rn(__dmul_rn(sx, px), __dmul_rn(sy, py)), __dmul_rn(sz, pz));
+    double nv = __dadd_rn(__dadd_rn(__dmul_rn(dx, qx), __dmul_rn(dy, qy)), __dmul_rn(dz, qz));
+    double nt = __dadd_rn(__dadd_rn(__dmul_rn(e2x, qx), __dmul_rn(e2y, qy)), __dmul_rn(e2z, qz));
+    if (det < 0.0) {
+        det = -det;
+        nu = -nu;
+        nv = -nv;
+        nt = -nt;
+    }
+    const int hit = (det > 0.0) && (nu >= 0.0) && (nv >= 0.0) && (__dadd_rn(nu, nv) <= det) &&
+                    (nt >= 0.0) && (nt <= det);
+    if (hit && tuv) {
+        tuv[0] = __ddiv_rn(nt, det);
+        tuv[1] = __ddiv_rn(nu, det);
+        tuv[2] = __ddiv_rn(nv, det);
+    }
+    return hit;
+}
+
+}  // namespace rsi

@@ -1,0 +1,135 @@
+// Single-mesh traversal launch (arXiv 2209.02878, Sec. 3.3
+// bvhIntersectionKernel): a persistent grid sized from the occupancy query
+// (the paper's N_grid lesson, Sec. 3.3: fill the machine), each warp pulling
+// 32 segments at a time from an atomic counter, the top treelet staged once
+// per block in shared memory.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "rsi_trace.h"
+#include "traverse_core.cuh"
+
+namespace rsi {
+
+template <int MODE, int STACK, bool STATS>
+__global__ void k_trace(TraceParams P) {
+    extern __shared__ float4 snodes[];
+    int S = 0;
+    if (P.smem_nodes > 0) {
+        S = min(P.smem_nodes, *P.treelet_n);
+        for (int q = threadIdx.x; q < 4 * S; q += blockDim.x) snodes[q] = P.treelet[q];
+        __syncthreads();
+    }
+    TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull};
+    unsigned long long segs = 0;
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long base = 0ull;
+        if (lane == 0) base = atomicAdd(P.work, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= (unsigned long long)P.nR) break;
+        const int64_t i = (int64_t)base + lane;
+        if (STATS && i < P.nR) ++segs;
+        process_segment<MODE, STACK, STATS>(P.A, P.B, P.nR, i, P.root, P.nodes, P.tris, P.treelet,
+                                            snodes, S, P.out, st);
+    }
+    if (STATS) flush_stats(st, P.stats, segs);
+}
+
+using KernelFn = void (*)(TraceParams);
+
+template <int MODE, bool STATS>
+static KernelFn pick_stack(int stack) {
+    switch (stack) {
+        case 16: return k_trace<MODE, 16, STATS>;
+        case 32: return k_trace<MODE, 32, STATS>;
+        default: return k_trace<MODE, 64, STATS>;
+    }
+}
+
+KernelFn trace_kernel(int mode, int stack, bool stats) {
+    if (stats) {
+        if (mode == RSI_MODE_BOOL) return pick_stack<RSI_MODE_BOOL, true>(stack);
+        if (mode == RSI_MODE_COUNT) return pick_stack<RSI_MODE_COUNT, true>(stack);
+        return pick_stack<RSI_MODE_NEAREST, true>(stack);
+    }
+    if (mode == RSI_MODE_BOOL) return pick_stack<RSI_MODE_BOOL, false>(stack);
+    if (mode == RSI_MODE_COUNT) return pick_stack<RSI_MODE_COUNT, false>(stack);
+    return pick_stack<RSI_MODE_NEAREST, false>(stack);
+}
+
+struct OccKey {
+    const void* fn;
+    int block, smem, dev;
+};
+static std::mutex g_occ_mu;
+static OccKey g_occ_key[64];
+static int g_occ_val[64];
+static int g_occ_n = 0;
+
+int sm_count(int dev) {
+    static int cache[64] = {0};
+    if (dev < 0 || dev >= 64) return 1;
+    if (cache[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
+}
+
+cudaError_t occupancy_grid(const void* fn, int block, int smem, int* grid) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        for (int k = 0; k < g_occ_n; ++k)
+            if (g_occ_key[k].fn == fn && g_occ_key[k].block == block &&
+                g_occ_key[k].smem == smem && g_occ_key[k].dev == dev) {
+                *grid = g_occ_val[k];
+                return cudaSuccess;
+            }
+    }
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem);
+    if (e != cudaSuccess) return e;
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    const int g = nb * sm_count(dev);
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    if (g_occ_n < 64) {
+        g_occ_key[g_occ_n] = OccKey{fn, block, smem, dev};
+        g_occ_val[g_occ_n] = g;
+        ++g_occ_n;
+    }
+    *grid = g;
+    return cudaSuccess;
+}
+
+cudaError_t launch_trace(const TraceParams& P, int mode, int stack, bool stats, int block,
+                         cudaStream_t s) {
+    KernelFn fn = trace_kernel(mode, stack, stats);
+    const int smem = P.smem_nodes > 0 ? P.smem_nodes * 64 : 0;
+    int grid = 0;
+    cudaError_t e = occupancy_grid((const void*)fn, block, smem, &grid);
+    if (e != cudaSuccess) return e;
+    const int64_t warps_needed = (P.nR + 31) / 32;
+    const int64_t blocks_needed = (warps_needed + block / 32 - 1) / (block / 32);
+    if (blocks_needed < grid) grid = (int)blocks_needed;
+    if (grid < 1) grid = 1;
+    e = cudaMemsetAsync(P.work, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (P.out.hit_idx) {
+        e = cudaMemsetAsync(P.out.n_hits, 0, sizeof(int64_t), s);
+        if (e != cudaSuccess) return e;
+    }
+    fn<<<grid, block, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace rsi

@@ -1,0 +1,81 @@
+"""Autotuner front end: runs rsi_autotune (the timing loop lives in the
+library) and keeps a JSON cache keyed by (GPU name, mode, N_t bucket, N_r
+bucket), so a workload class is tuned once per GPU model."""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import math
+import os
+
+import torch
+
+from . import _abi
+from . import _mode, _rsi_output, _alloc_outputs, _stream, _vp
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rsi_gb300", "tune.json")
+
+
+def bucket(n: int) -> int:
+    """Power-of-two bucket of a size."""
+    return 0 if n <= 0 else int(math.log2(n))
+
+
+def cache_key(mode, n_tri: int, n_seg: int, device=None) -> str:
+    name = torch.cuda.get_device_name(device)
+    return f"{name}|{mode}|t{bucket(n_tri)}|r{bucket(n_seg)}"
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def autotune(bvh, V, T, A, B, mode="bool", block_sizes=(64, 128, 256, 512),
+             stack_depths=(32, 64), smem_nodes=(-1, 255, 511, 1023), leaf_sizes=(1, 2, 4),
+             reps=5, cache: str | None = DEFAULT_CACHE, stream=None):
+    """Time every combination (the handle is rebuilt per leaf size) and
+    return (best launch options dict, best leaf size, table of entries).
+    The handle is left built with the best leaf size."""
+    lib = _abi.load()
+    m = _mode(mode)
+    key = cache_key(m, bvh.nT, int(A.shape[0]), A.device)
+    if cache:
+        hit = _load(cache).get(key)
+        if hit:  # the caller rebuilds with hit["leaf_size"] if it differs
+            return hit["launch"], hit["leaf_size"], hit.get("table", [])
+    o = _alloc_outputs(m, int(A.shape[0]), A.device, False, None)
+    ro = _rsi_output(o)
+
+    def arr(xs):
+        return (C.c_int32 * len(xs))(*xs), len(xs)
+
+    bs, nbs = arr(block_sizes)
+    sd, nsd = arr(stack_depths)
+    sm, nsm = arr(smem_nodes)
+    ls, nls = arr(leaf_sizes)
+    cap = nbs * nsd * nsm * nls
+    table = (_abi.rsi_tune_entry * cap)()
+    n_written = C.c_int32()
+    best = _abi.rsi_launch_opts()
+    best_leaf = C.c_int32()
+    with torch.cuda.device(A.device):
+        _abi.check(lib.rsi_autotune(bvh._h, _vp(V), _vp(T), _vp(A), _vp(B), int(A.shape[0]), m,
+                                    C.byref(ro), bs, nbs, sd, nsd, sm, nsm, ls, nls, int(reps),
+                                    _stream(stream), table, cap, C.byref(n_written),
+                                    C.byref(best), C.byref(best_leaf)), "rsi_autotune")
+    rows = [dict(block_size=t.block_size, stack_depth=t.stack_depth, smem_nodes=t.smem_nodes,
+                 leaf_size=t.leaf_size, ms=t.ms) for t in table[:n_written.value]]
+    launch = dict(block_size=best.block_size, stack_depth=best.stack_depth,
+                  smem_nodes=best.smem_nodes)
+    bvh.leaf_size = best_leaf.value
+    if cache:
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        data = _load(cache)
+        data[key] = dict(launch=launch, leaf_size=best_leaf.value, table=rows)
+        with open(cache, "w") as f:
+            json.dump(data, f, indent=1)
+    return launch, best_leaf.value, rows

@@ -1,0 +1,140 @@
+"""GPU adjoint (rsi_intersect_backward through RSIFunction) against the FP64
+CPU adjoint and FP64 central finite differences, on the differentiable
+workload: 257x257 heightfield (131,072 triangles), 262,144 near-vertical
+segments, loss = sum_i w_i . P_i with w ~ N(0, I3)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2209_02878_gb300 as rsi
+from paper_2209_02878_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def rel_l2(g, ref):
+    return float(np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30))
+
+
+def elementwise_ok(g, ref, idx, rel=1e-5):
+    scale = np.maximum(np.abs(ref[idx]), 1e-3 * np.abs(ref).max())
+    return np.abs(g[idx] - ref[idx]) <= rel * scale
+
+
+@pytest.fixture(scope="module")
+def diff_case():
+    mesh, seg, w = synth.workload_diff()
+    assert mesh.n_tri == 131072 and seg.n == 262144
+    ref = oracle.CpuBVH(mesh.V, mesh.T).query(seg.A, seg.B)
+    V = dev(mesh.V).requires_grad_(True)
+    A = dev(seg.A).requires_grad_(True)
+    B = dev(seg.B).requires_grad_(True)
+    P, tuv, tri = rsi.nearest_hit(V, dev(mesh.T), A, B)
+    loss = (P * dev(w)).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    got = dict(tri=tri.cpu().numpy(), P=P.detach().cpu().numpy(),
+               gV=V.grad.cpu().numpy().astype(np.float64),
+               gA=A.grad.cpu().numpy().astype(np.float64),
+               gB=B.grad.cpu().numpy().astype(np.float64))
+    gV, gA, gB = oracle.backward(mesh.V, mesh.T, seg.A, seg.B, ref["tri"], gP=w.astype(np.float64))
+    return mesh, seg, w, ref, got, dict(gV=gV, gA=gA, gB=gB)
+
+
+def test_forward_ids_match(diff_case):
+    mesh, seg, w, ref, got, _ = diff_case
+    np.testing.assert_array_equal(got["tri"], ref["tri"])
+    assert (ref["tri"] >= 0).mean() > 0.99
+
+
+@pytest.mark.parametrize("key", ["gV", "gA", "gB"])
+def test_adjoint_vs_fp64_adjoint(diff_case, key):
+    _, _, _, _, got, adj = diff_case
+    assert rel_l2(got[key], adj[key]) <= 1e-5
+    rng = np.random.default_rng(0)
+    flat_g, flat_r = got[key].ravel(), adj[key].ravel()
+    nz = np.nonzero(flat_r)[0]
+    idx = rng.choice(nz, min(1000, nz.size), replace=False)
+    assert elementwise_ok(flat_g, flat_r, idx).all()
+
+
+def test_adjoint_vs_finite_differences(diff_case):
+    mesh, seg, w, ref, got, adj = diff_case
+    tri = np.where(ref["neardeg"] == 0, ref["tri"], -1).astype(np.int32)
+    V64, A64, B64 = (mesh.V.astype(np.float64), seg.A.astype(np.float64),
+                     seg.B.astype(np.float64))
+    rng = np.random.default_rng(1)
+    w64 = w.astype(np.float64)
+
+    def loss(Vx, Ax, Bx, idx):
+        r = oracle.eval_fixed(Vx, mesh.T, Ax[idx], Bx[idx], tri[idx])
+        return float(np.sum(r[:, 3:] * w64[idx]))
+
+    # vertex -> segments whose crossing triangle uses it
+    hit = np.nonzero(tri >= 0)[0]
+    corners = mesh.T[tri[hit]]
+    order = np.argsort(corners.ravel(), kind="stable")
+    keys = corners.ravel()[order]
+    segs_of = hit[order // 3]
+    used = np.unique(keys)
+    checks = []
+    for vtx in rng.choice(used, 200, replace=False):
+        lo, hi = np.searchsorted(keys, vtx), np.searchsorted(keys, vtx, side="right")
+        sidx = segs_of[lo:hi]
+        for k in range(3):
+            h = 1e-6 * max(1.0, abs(V64[vtx, k]))
+            Vp, Vm = V64.copy(), V64.copy()
+            Vp[vtx, k] += h
+            Vm[vtx, k] -= h
+            fd = (loss(Vp, A64, B64, sidx) - loss(Vm, A64, B64, sidx)) / (2 * h)
+            checks.append((fd, got["gV"][vtx, k], adj["gV"][vtx, k]))
+    for i in rng.choice(hit, 70, replace=False):
+        for which, key in ((A64, "gA"), (B64, "gB")):
+            for k in range(3):
+                h = 1e-6 * max(1.0, abs(which[i, k]))
+                o = which[i, k]
+                which[i, k] = o + h
+                lp = loss(V64, A64, B64, [i])
+                which[i, k] = o - h
+                lm = loss(V64, A64, B64, [i])
+                which[i, k] = o
+                checks.append(((lp - lm) / (2 * h), got[key][i, k], adj[key][i, k]))
+    c = np.array(checks)
+    assert len(c) >= 1000
+    gmax = max(np.abs(got["gV"]).max(), np.abs(got["gA"]).max(), np.abs(got["gB"]).max())
+    # FP64 adjoint vs FD (the oracle's own pin, at this size)
+    assert np.all(np.abs(c[:, 2] - c[:, 0]) <= 1e-6 * np.maximum(np.abs(c[:, 0]), 1e-3 * gmax) + 1e-9)
+    # GPU vs FD
+    assert np.all(np.abs(c[:, 1] - c[:, 0]) <= 1e-5 * np.maximum(np.abs(c[:, 0]), 1e-3 * gmax))
+
+
+def test_translation_invariance(diff_case):
+    _, _, w, ref, got, _ = diff_case
+    total = got["gV"].sum(0) + got["gA"].sum(0) + got["gB"].sum(0)
+    want = w[ref["tri"] >= 0].astype(np.float64).sum(0)
+    assert np.allclose(total, want, rtol=1e-4, atol=1e-2)
+
+
+def test_sharded_backward_sums_to_unsharded(diff_case):
+    """Segments split into shards (as ranks would hold them): the per-shard
+    vertex gradients summed equal the unsharded gradient (the all-reduce a
+    multi-GPU run would do)."""
+    mesh, seg, w, ref, got, _ = diff_case
+    V, T = dev(mesh.V), dev(mesh.T)
+    tri = dev(ref["tri"])
+    bvh = rsi.BVH(V, T)
+    o = bvh.intersect(dev(seg.A), dev(seg.B), "nearest")
+    acc = torch.zeros_like(V)
+    for sl in np.array_split(np.arange(seg.n), 4):
+        s = slice(int(sl[0]), int(sl[-1]) + 1)
+        rsi.intersect_backward(V, T, dev(seg.A[s]), dev(seg.B[s]), o["tri"][s].contiguous(),
+                               o["tuv"][s].contiguous(), grad_point=dev(w[s]), grad_V=acc)
+    torch.cuda.synchronize()
+    assert rel_l2(acc.cpu().numpy().astype(np.float64), got["gV"]) <= 1e-6
+    assert torch.equal(o["tri"], tri)

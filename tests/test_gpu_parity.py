@@ -1,0 +1,296 @@
+"""GPU parity: the CUDA path (through the C ABI binding) against the FP64 CPU
+oracle, element by element on the same seeded inputs.
+
+Flags, counts and triangle ids must match bit-exactly (the kernels recompute
+every decision their FP32 error bound cannot settle in FP64 with the
+definition's operation order); (t, u, v), points and distances within
+relative 1e-5 of the oracle's FP64 values (|x - x_ref| <= 1e-5 max(1,|x_ref|)).
+Near-degenerate segments are counted and must match too."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2209_02878_gb300 as rsi
+from paper_2209_02878_gb300 import synth
+
+from _util import assert_close, tree_check
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def run_all_modes(bvh, A, B, launch=None, compact=False):
+    o = {m: bvh.intersect(A, B, m, launch=launch, compact=compact) for m in ("bool", "count", "nearest")}
+    torch.cuda.synchronize()
+    return {m: {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in d.items()}
+            for m, d in o.items()}
+
+
+def compare(got, ref, idx=None, what=""):
+    sel = slice(None) if idx is None else idx
+    np.testing.assert_array_equal(got["bool"]["flag"], ref["flag"][sel], err_msg=what + " flag")
+    np.testing.assert_array_equal(got["count"]["count"], ref["count"][sel], err_msg=what + " count")
+    np.testing.assert_array_equal(got["nearest"]["tri"], ref["tri"][sel], err_msg=what + " tri")
+    assert_close(got["nearest"]["tuv"], ref["tuv"][sel], what=what + " tuv")
+    assert_close(got["nearest"]["point"], ref["point"][sel], what=what + " point")
+    assert_close(got["nearest"]["dist"], ref["dist"][sel], what=what + " dist")
+
+
+# ------------------------------------------------------------ small, full
+@pytest.fixture(scope="module")
+def small():
+    mesh, seg = synth.workload_small_bool()
+    ref = oracle.brute(mesh.V, mesh.T, seg.A, seg.B)
+    return mesh, seg, ref
+
+
+def test_small_heightfield_all_modes(small):
+    mesh, seg, ref = small
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    got = run_all_modes(bvh, dev(seg.A), dev(seg.B))
+    compare(got, ref, what="1922 tris x 10k")
+    assert bvh.status() == 0
+    assert ref["flag"].mean() > 0.3  # the workload does cross the surface
+
+
+@pytest.mark.parametrize("leaf,levels", [(1, 0), (1, -1), (2, 4), (4, 10), (8, 12)])
+def test_small_build_options(small, leaf, levels):
+    mesh, seg, ref = small
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T), leaf_size=leaf, top_levels=levels)
+    compare(run_all_modes(bvh, dev(seg.A), dev(seg.B)), ref, what=f"leaf {leaf} levels {levels}")
+    tree_check(bvh.export(), mesh.n_tri, leaf_size=leaf)
+
+
+@pytest.mark.parametrize("launch", [
+    dict(block_size=32), dict(block_size=128, smem_nodes=-1), dict(block_size=512),
+    dict(block_size=1024, smem_nodes=2047), dict(stack_depth=16), dict(stack_depth=32),
+    dict(smem_nodes=1)])
+def test_small_launch_options(small, launch):
+    mesh, seg, ref = small
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    compare(run_all_modes(bvh, dev(seg.A), dev(seg.B), launch=launch), ref, what=str(launch))
+
+
+def test_build_steps_match_definition(small):
+    mesh, _, _ = small
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    g = bvh.export()
+    r = oracle.lbvh(mesh.V, mesh.T)
+    np.testing.assert_array_equal(g["bounds"], r["bounds"])
+    np.testing.assert_array_equal(g["order"], r["order"].astype(np.int32))
+    np.testing.assert_array_equal(g["codes"], r["codes"][r["order"]])
+    np.testing.assert_array_equal(g["left"], r["left"])
+    np.testing.assert_array_equal(g["right"], r["right"])
+    np.testing.assert_array_equal(g["range"], r["range"])
+    np.testing.assert_array_equal(g["nbox"], r["nbox"])
+    np.testing.assert_array_equal(g["lbox"], r["lbox"])
+    tree_check(g, mesh.n_tri)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_build_steps_duplicate_codes(seed):
+    # clustered centroids force equal Morton codes (index tie-break)
+    rng = np.random.default_rng(seed)
+    n = 5000
+    base = rng.uniform(0, 1, size=(50, 3))
+    cen = base[rng.integers(0, 50, n)] + rng.normal(0, 1e-6, size=(n, 3))
+    V = (cen[:, None, :] + rng.normal(0, 1e-3, size=(n, 3, 3))).reshape(-1, 3).astype(np.float32)
+    T = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+    bvh = rsi.BVH(dev(V), dev(T))
+    g = bvh.export()
+    r = oracle.lbvh(V, T)
+    assert len(np.unique(r["codes"])) < n  # duplicates present
+    for k in ("left", "right", "range", "nbox", "lbox"):
+        np.testing.assert_array_equal(g[k], r[k], err_msg=k)
+    np.testing.assert_array_equal(g["order"], r["order"].astype(np.int32))
+    tree_check(g, n)
+    A = rng.uniform(-0.1, 1.1, size=(20000, 3)).astype(np.float32)
+    B = (A + rng.normal(0, 0.2, size=A.shape)).astype(np.float32)
+    compare(run_all_modes(bvh, dev(A), dev(B)), oracle.brute(V, T, A, B), what="clustered")
+
+
+def test_icosphere_build_and_counts():
+    rng = np.random.default_rng(7)
+    mesh = synth.icosphere(4, rng)
+    seg = synth.segments_box(rng, 20000, [-1.5] * 3, [1.5] * 3, [-1.5] * 3, [1.5] * 3)
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    g = bvh.export()
+    r = oracle.lbvh(mesh.V, mesh.T)
+    for k in ("left", "right", "range", "nbox", "lbox"):
+        np.testing.assert_array_equal(g[k], r[k], err_msg=k)
+    ref = oracle.brute(mesh.V, mesh.T, seg.A, seg.B)
+    compare(run_all_modes(bvh, dev(seg.A), dev(seg.B)), ref, what="icosphere L4")
+    assert ref["count"].max() >= 2
+
+
+# ------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("nR", [1, 31, 32, 33, 1007])
+@pytest.mark.parametrize("nT", [1, 2, 3, 17])
+def test_ragged_sizes(nR, nT):
+    rng = np.random.default_rng(nR * 100 + nT)
+    mesh, seg = synth.random_soup(rng, nT, nR)
+    ref = oracle.brute(mesh.V, mesh.T, seg.A, seg.B)
+    for leaf in (1, 4):
+        bvh = rsi.BVH(dev(mesh.V), dev(mesh.T), leaf_size=leaf)
+        compare(run_all_modes(bvh, dev(seg.A), dev(seg.B)), ref, what=f"nT={nT} nR={nR}")
+        tree_check(bvh.export(), nT, leaf_size=leaf)
+
+
+def test_empty_inputs():
+    V = dev(np.zeros((3, 3), np.float32))
+    T = dev(np.zeros((0, 3), np.int32))
+    A = dev(np.zeros((5, 3), np.float32))
+    B = dev(np.ones((5, 3), np.float32))
+    bvh = rsi.BVH(V, T)
+    got = run_all_modes(bvh, A, B, compact=True)
+    assert not got["bool"]["flag"].any() and not got["count"]["count"].any()
+    assert np.all(got["nearest"]["tri"] == -1)
+    assert got["nearest"]["n_hits"][0] == 0
+    mesh, _ = synth.workload_small_bool()
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    e = dev(np.zeros((0, 3), np.float32))
+    got = run_all_modes(bvh, e, e)
+    assert got["bool"]["flag"].size == 0
+
+
+def test_degenerate_and_special_segments():
+    mesh, seg = synth.workload_small_bool(n_seg=2000)
+    V = mesh.V.copy()
+    T = mesh.T.copy()
+    # degenerate triangles: collapse some (zero edge) and flatten others (collinear)
+    T[5] = [T[5][0], T[5][0], T[5][1]]
+    T[9] = [0, 1, 2]
+    V_extra = np.array([[0.5, 0.5, 0.0], [0.6, 0.5, 0.0], [0.7, 0.5, 0.0]], np.float32)
+    T = np.concatenate([T, np.array([[len(V), len(V) + 1, len(V) + 2]], np.int32)])
+    V = np.concatenate([V, V_extra])
+    # duplicate triangle (tie on t: lower index wins)
+    T = np.concatenate([T, T[100:101]])
+    A, B = seg.A.copy(), seg.B.copy()
+    A[0] = [np.nan, 0.5, -1]
+    B[1] = [np.inf, 0.5, 1]
+    A[2] = B[2]                                   # zero-length segment
+    A[3], B[3] = V[T[100][0]], V[T[100][1]]      # along a triangle edge
+    A[4] = V[T[200][0]] - [0, 0, 0.5]            # through a vertex
+    B[4] = V[T[200][0]] + [0, 0, 0.5]
+    c = V[T[100]].mean(0)                         # through the duplicated triangle
+    A[5], B[5] = c - [0, 0, 0.5], c + [0, 0, 0.5]
+    A[6], B[6] = [1e-25, 0.3, 0.5], [2e-25, 0.3, -0.5]       # |d_x| < 2^-60
+    ref = oracle.brute(V, T, A, B)
+    bvh = rsi.BVH(dev(V), dev(T))
+    compare(run_all_modes(bvh, dev(A), dev(B)), ref, what="special")
+    assert ref["tri"][5] == 100 and ref["count"][5] >= 2
+
+
+def test_bad_index_sets_status():
+    mesh, seg = synth.workload_small_bool(n_seg=100)
+    T = mesh.T.copy()
+    T[7, 1] = len(mesh.V) + 5
+    T[8, 0] = -1
+    bvh = rsi.BVH(dev(mesh.V), dev(T))
+    o = bvh.intersect(dev(seg.A), dev(seg.B), "count")
+    assert bvh.status() == 4          # RSI_ERR_BAD_INDEX
+    assert bvh.status() == 0          # cleared
+    # the bad triangles never hit (the oracle sees them as degenerate)
+    good = np.ones(len(T), bool)
+    good[[7, 8]] = False
+    ref = oracle.brute(mesh.V, np.where(good[:, None], T, 0), seg.A, seg.B)
+    np.testing.assert_array_equal(o["count"].cpu().numpy(), ref["count"])
+
+
+def test_compaction(small):
+    mesh, seg, ref = small
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    got = run_all_modes(bvh, dev(seg.A), dev(seg.B), compact=True)
+    for m in ("count", "nearest"):
+        g = got[m]
+        n = int(g["n_hits"][0])
+        assert n == int((ref["count"] > 0).sum())
+        idx = g["hit_idx"][:n]
+        assert np.array_equal(np.sort(idx), np.nonzero(ref["count"] > 0)[0])
+        if m == "count":
+            np.testing.assert_array_equal(g["hit_count"][:n], ref["count"][idx])
+        else:
+            np.testing.assert_array_equal(g["hit_tri"][:n], ref["tri"][idx])
+            assert_close(g["hit_dist"][:n], ref["dist"][idx], what="hit_dist")
+            assert_close(g["hit_point"][:n], ref["point"][idx], what="hit_point")
+    # capacity smaller than the number of hits: total still counted, no overrun
+    o = bvh.intersect(dev(seg.A), dev(seg.B), "nearest", compact=True, hit_cap=7)
+    torch.cuda.synchronize()
+    assert int(o["n_hits"][0]) == int((ref["count"] > 0).sum())
+
+
+def test_stats_counters(small):
+    mesh, seg, ref = small
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    o = bvh.intersect(dev(seg.A), dev(seg.B), "count", stats=True)
+    st = o["stats"]
+    assert st["segments"] == seg.n
+    assert st["tri_tests"] >= ref["count"].sum()
+    assert st["node_visits"] >= seg.n
+    assert st["fp64_tests"] <= 0.01 * st["tri_tests"] + 10
+    np.testing.assert_array_equal(o["count"].cpu().numpy(), ref["count"])
+
+
+def test_refit_moves_with_vertices(small):
+    mesh, seg, _ = small
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    rng = np.random.default_rng(3)
+    V2 = (mesh.V + rng.normal(0, 0.02, size=mesh.V.shape)).astype(np.float32)
+    bvh.refit(dev(V2))
+    ref = oracle.brute(V2, mesh.T, seg.A, seg.B)
+    compare(run_all_modes(bvh, dev(seg.A), dev(seg.B)), ref, what="refit")
+    tree_check(bvh.export(), mesh.n_tri)
+
+
+# ------------------------------------------------------------ full sizes
+@pytest.fixture(scope="module")
+def paper_scale():
+    mesh, seg = synth.workload_paper_bool()
+    return mesh, seg
+
+
+def test_paper_scale_bool_sampled(paper_scale):
+    """29,768 triangles x 10M segments in the benchmark's launch
+    configuration; 20k sampled segments against brute force."""
+    mesh, seg = paper_scale
+    assert mesh.n_tri == 29768 and seg.n == 10_000_000
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    A, B = dev(seg.A), dev(seg.B)
+    flag = bvh.intersect(A, B, "bool")["flag"].cpu().numpy()
+    cnt = bvh.intersect(A, B, "count")["count"].cpu().numpy()
+    assert np.array_equal(flag, (cnt > 0).astype(np.uint8))      # holds at any size
+    idx = np.random.default_rng(0).choice(seg.n, 20000, replace=False)
+    ref = oracle.brute(mesh.V, mesh.T, seg.A[idx], seg.B[idx])
+    np.testing.assert_array_equal(flag[idx], ref["flag"])
+    np.testing.assert_array_equal(cnt[idx], ref["count"])
+    assert 0.05 < flag.mean() < 0.95
+
+
+def test_sphere_scale_count_nearest_sampled():
+    """1,310,720-triangle icosphere x 1M segments, count + nearest; 1500
+    sampled segments against brute force, parity invariant on all."""
+    mesh, seg = synth.workload_sphere()
+    assert mesh.n_tri == 1_310_720 and mesh.n_vert == 655_362
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    A, B = dev(seg.A), dev(seg.B)
+    cnt = bvh.intersect(A, B, "count")["count"].cpu().numpy()
+    o = bvh.intersect(A, B, "nearest", compact=True)
+    tri = o["tri"].cpu().numpy()
+    assert np.array_equal(tri >= 0, cnt > 0)
+    assert int(o["n_hits"][0].item()) == int((cnt > 0).sum())
+    idx = np.random.default_rng(1).choice(seg.n, 1500, replace=False)
+    ref = oracle.brute(mesh.V, mesh.T, seg.A[idx], seg.B[idx])
+    np.testing.assert_array_equal(cnt[idx], ref["count"])
+    np.testing.assert_array_equal(tri[idx], ref["tri"])
+    assert_close(o["tuv"].cpu().numpy()[idx], ref["tuv"], what="tuv")
+    assert_close(o["point"].cpu().numpy()[idx], ref["point"], what="point")
+    # closed surface: both ends outside the bounding sphere -> even count
+    rmax = np.linalg.norm(mesh.V.astype(np.float64), axis=1).max()
+    out = (np.linalg.norm(seg.A, axis=1) > rmax) & (np.linalg.norm(seg.B, axis=1) > rmax)
+    assert np.all(cnt[out] % 2 == 0)
+    assert cnt.max() >= 4

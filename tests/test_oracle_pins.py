@@ -89,6 +89,19 @@ def test_nan_segment_is_miss(orc):
     assert o["flag"][0] == 0 and o["tri"][0] == -1
 
 
+def test_non_finite_never_hits(orc):
+    # without the rule, an infinite start gives det = nT = inf and a "hit"
+    V = np.array(UNIT, np.float32)
+    T = np.array([[0, 1, 2]])
+    A = np.array([[0.25, 0.25, -np.inf], [0.25, 0.25, -1]], np.float32)
+    B = np.array([[0.25, 0.25, 1], [0.25, 0.25, 1]], np.float32)
+    o = orc.brute(V, T, A, B)
+    assert list(o["flag"]) == [0, 1]
+    V2 = V.copy()
+    V2[1, 0] = np.inf
+    assert orc.brute(V2, T, A[1:], B[1:])["flag"][0] == 0
+
+
 def test_nearest_tie_goes_to_lower_index(orc):
     # two copies of the same triangle: equal t, the smaller index wins
     V = np.array(UNIT, np.float32)
