@@ -62,7 +62,10 @@ typedef enum {
     RSI_ERR_BAD_INDEX = 4,      /* a triangle index is outside [0, nV) */
     RSI_ERR_STACK_OVERFLOW = 5, /* traversal stack too small (never with depth >= 64) */
     RSI_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
-    RSI_ERR_NOT_BUILT = 7       /* handle has no built tree */
+    RSI_ERR_NOT_BUILT = 7,      /* handle has no built tree */
+    RSI_ERR_INTERNAL = 8        /* a device-side consistency bound was hit (a
+                                   climb longer than any radix tree, or more
+                                   node visits than nodes); the work stopped */
 } rsi_status;
 
 typedef enum {

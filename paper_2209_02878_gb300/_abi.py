@@ -20,6 +20,7 @@ RSI_ERR_BAD_INDEX = 4
 RSI_ERR_STACK_OVERFLOW = 5
 RSI_ERR_TIMEOUT = 6
 RSI_ERR_NOT_BUILT = 7
+RSI_ERR_INTERNAL = 8
 
 RSI_MODE_BOOL = 0
 RSI_MODE_COUNT = 1

@@ -167,6 +167,7 @@ const char* rsi_status_string(rsi_status s) {
         case RSI_ERR_STACK_OVERFLOW: return "traversal stack overflow";
         case RSI_ERR_TIMEOUT: return "device-side wait timed out";
         case RSI_ERR_NOT_BUILT: return "tree not built";
+        case RSI_ERR_INTERNAL: return "device-side consistency bound hit";
     }
     return "unknown status";
 }
@@ -397,6 +398,8 @@ static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, in
     P.smem_nodes = c.smem_nodes;
     P.work = h->scratch;
     P.stats = h->scratch + 1;
+    P.max_visits = (int)h->nT + 2;
+    P.status = h->tb.status;
     P.out = trav_out(mode, out);
     if (c.stats) RSI_CK(cudaMemsetAsync(P.stats, 0, 6 * 8, (cudaStream_t)s));
     RSI_CK(rsi::launch_trace(P, mode, c.stack, c.stats, c.block, (cudaStream_t)s));
@@ -603,6 +606,8 @@ rsi_status rsi_batch_intersect(rsi_batch b, rsi_stream s) {
     P.nodes = b->tb.nodes;
     P.tris = b->tb.tris;
     P.work = b->work;
+    P.max_visits = b->tb.N + 2;
+    P.status = b->tb.status;
     RSI_CK(rsi::launch_batch(P, b->cfg.block, b->cfg.stack, (cudaStream_t)s));
     return RSI_OK;
 }

@@ -35,17 +35,20 @@ __global__ void k_batch(BatchParams P) {
             case RSI_MODE_BOOL:
                 process_segment<RSI_MODE_BOOL, STACK, false>(it.A, it.B, it.nR, i, it.root,
                                                              P.nodes, P.tris, nullptr, nullptr,
-                                                             0, it.out, st);
+                                                             0, P.max_visits, P.status,
+                                                             it.out, st);
                 break;
             case RSI_MODE_COUNT:
                 process_segment<RSI_MODE_COUNT, STACK, false>(it.A, it.B, it.nR, i, it.root,
                                                               P.nodes, P.tris, nullptr, nullptr,
-                                                              0, it.out, st);
+                                                              0, P.max_visits, P.status,
+                                                              it.out, st);
                 break;
             default:
                 process_segment<RSI_MODE_NEAREST, STACK, false>(it.A, it.B, it.nR, i, it.root,
                                                                 P.nodes, P.tris, nullptr,
-                                                                nullptr, 0, it.out, st);
+                                                                nullptr, 0, P.max_visits,
+                                                                P.status, it.out, st);
                 break;
         }
     }

@@ -276,11 +276,12 @@ __global__ void k_karras(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ 
     }
     const int d = kdelta(keys, off, n, i, i + 1) > kdelta(keys, off, n, i, i - 1) ? 1 : -1;
     const int dmin = kdelta(keys, off, n, i, i - d);
-    int lmax = 2;
-    while (kdelta(keys, off, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t lmax = 2;  // stops once i + lmax d leaves [0, n)
+    while (kdelta(keys, off, n, i, (int)max((int64_t)-1, min((int64_t)n, i + lmax * d))) > dmin)
+        lmax <<= 1;
     int l = 0;
-    for (int t = lmax >> 1; t >= 1; t >>= 1)
-        if (kdelta(keys, off, n, i, i + (l + t) * d) > dmin) l += t;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (l + t < n && kdelta(keys, off, n, i, i + (int)(l + t) * d) > dmin) l += (int)t;
     const int j = i + l * d;
     const int dn = kdelta(keys, off, n, i, j);
     int s = 0, t = l;
@@ -371,7 +372,12 @@ __global__ void k_climb(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ k
         return;
     }
     int node = tb.parent[N + g];
-    while (true) {
+    // a radix tree over 62-bit keys is at most 63 levels deep
+    for (int climb = 0;; ++climb) {
+        if (climb > 70 || node < off || node >= off + n - 1) {
+            latch(tb.status, RSI_ERR_INTERNAL);
+            return;
+        }
         __threadfence();
         if (atomicAdd(&tb.flag[node], 1) == 0) return;  // the sibling finishes this node
         __threadfence();

@@ -20,6 +20,8 @@ struct TraceParams {
     int smem_nodes;
     unsigned long long* work;   // zeroed before each launch
     unsigned long long* stats;  // 6 counters (STATS launches)
+    int max_visits;             // node fetches per segment before giving up
+    int32_t* status;
     TravOut out;
 };
 
@@ -54,6 +56,8 @@ struct BatchParams {
     const float4* nodes;
     const float4* tris;
     unsigned long long* work;
+    int max_visits;
+    int32_t* status;
 };
 
 cudaError_t launch_batch(const BatchParams& P, int block, int stack, cudaStream_t s);

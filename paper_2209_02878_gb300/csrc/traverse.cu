@@ -32,7 +32,7 @@ __global__ void k_trace(TraceParams P) {
         const int64_t i = (int64_t)base + lane;
         if (STATS && i < P.nR) ++segs;
         process_segment<MODE, STACK, STATS>(P.A, P.B, P.nR, i, P.root, P.nodes, P.tris, P.treelet,
-                                            snodes, S, P.out, st);
+                                            snodes, S, P.max_visits, P.status, P.out, st);
     }
     if (STATS) flush_stats(st, P.stats, segs);
 }

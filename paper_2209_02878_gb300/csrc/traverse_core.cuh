@@ -132,12 +132,18 @@ __device__ __forceinline__ bool trace(const Seg& s, const float* A, const float*
                                       int root, const float4* __restrict__ nodes,
                                       const float4* __restrict__ tris,
                                       const float4* __restrict__ treelet, const float4* snodes,
-                                      int S, Result& res, TravStats& st) {
+                                      int S, int max_visits, int32_t* status, Result& res,
+                                      TravStats& st) {
     int stack[STACK];
     int sp = 0;
     int node = root;
     float tlim = 1.f;
-    while (true) {
+    // each node of a tree is visited at most once per segment
+    for (int visits = 0;; ++visits) {
+        if (visits > max_visits) {
+            atomicCAS(status, 0, RSI_ERR_INTERNAL);
+            break;
+        }
         float4 n0, n1, n2, n3;
         if (node < 0) {
             const int k = ~node;
@@ -197,11 +203,13 @@ __device__ __noinline__ void trace_deep(const Seg& s, const float* A, const floa
                                         int root, const float4* __restrict__ nodes,
                                         const float4* __restrict__ tris,
                                         const float4* __restrict__ treelet, const float4* snodes,
-                                        int S, Result& res, TravStats& st) {
+                                        int S, int max_visits, int32_t* status, Result& res,
+                                        TravStats& st) {
     res.count = 0;
     res.best = -1;
     res.b64 = false;
-    trace<MODE, 64, STATS>(s, A, B, i, root, nodes, tris, treelet, snodes, S, res, st);
+    trace<MODE, 64, STATS>(s, A, B, i, root, nodes, tris, treelet, snodes, S, max_visits, status,
+                           res, st);
 }
 
 __device__ __forceinline__ void result_init(Result& r) {
@@ -317,7 +325,8 @@ __device__ __forceinline__ void process_segment(const float* A, const float* B, 
                                                 const float4* __restrict__ nodes,
                                                 const float4* __restrict__ tris,
                                                 const float4* __restrict__ treelet,
-                                                const float4* snodes, int S, const TravOut& o,
+                                                const float4* snodes, int S, int max_visits,
+                                                int32_t* status, const TravOut& o,
                                                 TravStats& st) {
     Result res;
     result_init(res);
@@ -328,11 +337,11 @@ __device__ __forceinline__ void process_segment(const float* A, const float* B, 
         const bool seg_ok = seg_setup(A, B, i, s);
         if (seg_ok && root != kNoRoot) {
             const bool ok = trace<MODE, STACK, STATS>(s, A, B, i, root, nodes, tris, treelet,
-                                                      snodes, S, res, st);
+                                                      snodes, S, max_visits, status, res, st);
             if (STACK < 64 && !ok) {
                 if (STATS) ++st.overflows;
-                trace_deep<MODE, STATS>(s, A, B, i, root, nodes, tris, treelet, snodes, S, res,
-                                        st);
+                trace_deep<MODE, STATS>(s, A, B, i, root, nodes, tris, treelet, snodes, S,
+                                        max_visits, status, res, st);
             }
         }
         write_result<MODE, STATS>(o, s, seg_ok, A, B, i, tris, res, dist, P, st);
