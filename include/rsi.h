@@ -87,17 +87,33 @@ typedef struct {
 /* Options of one traversal launch.  Zero-initialised = defaults. */
 typedef struct {
     int32_t block_size;  /* threads per block, multiple of 32 in [32, 1024]
-                            (0 -> 256) */
+                            (0 -> 128); capped at what the kernel's register
+                            use allows */
     int32_t stack_depth; /* per-segment traversal stack entries: 16, 32 or 64
                             (0 -> 64).  Radix trees over 64-bit keys are at
                             most 63 levels deep, so 64 never overflows; a
                             smaller stack re-runs overflowed segments with a
                             deeper one. */
     int32_t smem_nodes;  /* treelet nodes staged in shared memory per block
-                            (64 B each, at most 2048); 0 -> automatic (511);
-                            -1 -> none */
+                            (64 B each, at most 2048); 0 or -1 -> none (the
+                            top levels then live in L1, which measured
+                            faster on the paper-scale workload) */
     int32_t stats;       /* nonzero: count node visits, triangle tests and
-                            FP64 fallbacks (slower; see rsi_get_stats) */
+                            FP64 fallbacks (slower; see rsi_intersect_stats) */
+    int32_t sort_bits;   /* coherent segment order (the paper's Morton-sorted
+                            rays, Sec. 4.1): segments are processed in the
+                            order of a key of this many bits (midpoint Morton
+                            code + direction octant), 6..30; 0 or -1 -> input
+                            order (measured faster for random segments).
+                            Results do not depend on the order.  Needs a
+                            workspace of 16 B per segment, allocated by the
+                            handle on first use (cudaMallocAsync on s) and
+                            kept for later calls of the same or smaller nR. */
+    int32_t node_width;  /* traversal node arity: 2 (the binary tree, as in
+                            the paper) or 4 (each visit tests the four
+                            grandchildren of a binary node: half the chain of
+                            dependent node fetches, twice the box tests);
+                            0 -> 2.  smem_nodes > 0 implies 2. */
 } rsi_launch_opts;
 
 /* Per-segment outputs, all DEVICE pointers owned by the caller.  Which must be
@@ -240,25 +256,25 @@ rsi_status rsi_intersect_stats(rsi_bvh h, const float* dA, const float* dB, int6
 
 /* Adjoint of the NEAREST outputs with the crossing triangle held fixed (not
  * in the paper; implicit differentiation of a + t d = v0 + u e1 + v e2).
- * With M = [-d, e1, e2], x = (t,u,v), g_x = (gt + gP.d, gu, gv),
- * lambda = M^-T g_x:
+ * With M = [-d, e1, e2], x = (t,u,v) = M^-1 (a - v0) (recomputed in FP64
+ * from the geometry), g_x = (gt + gP.d, gu, gv), lambda = M^-T g_x:
  *   dA[i] = (1-t)(gP + lambda),  dB[i] = t (gP + lambda),
  *   dGradV[T[j][0]] += -(1-u-v) lambda, dGradV[T[j][1]] += -u lambda,
- *   dGradV[T[j][2]] += -v lambda   (atomic scatter-add),
- * and zero for segments with dTri[i] < 0.
- * Inputs: dV, dT as for the build; dA, dB the segments; dTri int32[nR] and
- * dTuv float[nR][3] saved from the NEAREST forward; dGradPoint float[nR][3]
- * and dGradTuv float[nR][3] (either may be NULL = zero).  Outputs:
- * dGradV float[nV][3] ACCUMULATED into (caller zeroes it), dGradA / dGradB
- * float[nR][3] overwritten (either may be NULL).  Errors: RSI_ERR_ARG,
- * RSI_ERR_CUDA; a dTri entry >= nT or a vertex index outside [0, nV) is
- * skipped. */
+ *   dGradV[T[j][2]] += -v lambda,
+ * and zero for segments with dTri[i] < 0.  The algebra and the vertex sums
+ * run in FP64 (atomic scatter-add into a stream-ordered FP64 scratch of
+ * 24 nV bytes, freed on s), rounded to FP32 once.
+ * Inputs: dV, dT as for the build; dA, dB the segments; dTri int32[nR] saved
+ * from the NEAREST forward; dGradPoint float[nR][3] and dGradTuv float[nR][3]
+ * (either may be NULL = zero).  Outputs: dGradV float[nV][3] ACCUMULATED into
+ * (caller zeroes it), dGradA / dGradB float[nR][3] overwritten (each may be
+ * NULL).  Errors: RSI_ERR_ARG, RSI_ERR_OOM, RSI_ERR_CUDA; a dTri entry >= nT
+ * or a vertex index outside [0, nV) contributes nothing. */
 rsi_status rsi_intersect_backward(const float* dV, int64_t nV, const int32_t* dT, int64_t nT,
                                   const float* dA, const float* dB, int64_t nR,
-                                  const int32_t* dTri, const float* dTuv,
-                                  const float* dGradPoint, const float* dGradTuv,
-                                  float* dGradV, float* dGradA, float* dGradB,
-                                  rsi_stream s);
+                                  const int32_t* dTri, const float* dGradPoint,
+                                  const float* dGradTuv, float* dGradV, float* dGradA,
+                                  float* dGradB, rsi_stream s);
 
 /* ------------------------------------------------------------ batched --- */
 

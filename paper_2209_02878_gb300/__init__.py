@@ -227,13 +227,13 @@ def intersect(V, T, A, B, mode="bool", **kw):
         bvh.close()
 
 
-def intersect_backward(V, T, A, B, tri, tuv, grad_point=None, grad_tuv=None, grad_V=None,
+def intersect_backward(V, T, A, B, tri, grad_point=None, grad_tuv=None, grad_V=None,
                        stream=None):
     """Adjoint of the nearest outputs with the triangle held fixed
     (rsi_intersect_backward).  Returns (grad_V, grad_A, grad_B); grad_V is
     accumulated into when given."""
     lib = _abi.load()
-    for t, nme in ((V, "V"), (A, "A"), (B, "B"), (tuv, "tuv")):
+    for t, nme in ((V, "V"), (A, "A"), (B, "B")):
         _check_tensor(t, nme, torch.float32)
     _check_tensor(T, "T", torch.int32)
     _check_tensor(tri, "tri", torch.int32, cols=0)
@@ -247,9 +247,9 @@ def intersect_backward(V, T, A, B, tri, tuv, grad_point=None, grad_tuv=None, gra
     gB = torch.empty_like(B)
     with torch.cuda.device(V.device):
         _abi.check(lib.rsi_intersect_backward(_vp(V), int(V.shape[0]), _vp(T), int(T.shape[0]),
-                                              _vp(A), _vp(B), n, _vp(tri), _vp(tuv),
-                                              _vp(grad_point), _vp(grad_tuv), _vp(gV), _vp(gA),
-                                              _vp(gB), _stream(stream)),
+                                              _vp(A), _vp(B), n, _vp(tri), _vp(grad_point),
+                                              _vp(grad_tuv), _vp(gV), _vp(gA), _vp(gB),
+                                              _stream(stream)),
                    "rsi_intersect_backward")
     return gV, gA, gB
 
@@ -264,14 +264,14 @@ class RSIFunction(torch.autograd.Function):
         if bvh is None:
             bvh = BVH(V.detach(), T)
         o = bvh.intersect(A.detach(), B.detach(), "nearest")
-        ctx.save_for_backward(V.detach(), A.detach(), B.detach(), T, o["tri"], o["tuv"])
+        ctx.save_for_backward(V.detach(), A.detach(), B.detach(), T, o["tri"])
         ctx.mark_non_differentiable(o["tri"])
         return o["point"], o["tuv"], o["tri"]
 
     @staticmethod
     def backward(ctx, g_point, g_tuv, g_tri):
-        V, A, B, T, tri, tuv = ctx.saved_tensors
-        gV, gA, gB = intersect_backward(V, T, A, B, tri, tuv, g_point, g_tuv)
+        V, A, B, T, tri = ctx.saved_tensors
+        gV, gA, gB = intersect_backward(V, T, A, B, tri, g_point, g_tuv)
         return (gV if ctx.needs_input_grad[0] else None,
                 gA if ctx.needs_input_grad[1] else None,
                 gB if ctx.needs_input_grad[2] else None, None, None)

@@ -39,7 +39,8 @@ class rsi_build_opts(C.Structure):
 
 
 class rsi_launch_opts(C.Structure):
-    _fields_ = [("block_size", i32), ("stack_depth", i32), ("smem_nodes", i32), ("stats", i32)]
+    _fields_ = [("block_size", i32), ("stack_depth", i32), ("smem_nodes", i32), ("stats", i32),
+                ("sort_bits", i32), ("node_width", i32)]
 
 
 class rsi_output(C.Structure):
@@ -84,7 +85,7 @@ _PROTOS = {
     "rsi_intersect_stats": (C.c_int, [vp, vp, vp, i64, C.c_int, P(rsi_output),
                                       P(rsi_launch_opts), vp, P(rsi_stats)]),
     "rsi_intersect_backward": (C.c_int, [vp, i64, vp, i64, vp, vp, i64, vp, vp, vp, vp, vp,
-                                         vp, vp, vp]),
+                                         vp, vp]),
     "rsi_batch_create": (C.c_int, [P(rsi_batch_item), i32, P(rsi_build_opts),
                                    P(rsi_launch_opts), vp, P(vp)]),
     "rsi_batch_build": (C.c_int, [vp, vp]),

@@ -31,8 +31,8 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build librsi")
 
 
-def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+def _sources(src_dir=None):
+    return sorted(glob.glob(os.path.join(src_dir or CSRC, "*.cu")))
 
 
 def _deps():
@@ -48,17 +48,22 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Build librsi.so if any source is newer; return its path."""
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra=(), out: str | None = None,
+          objdir: str | None = None, src_dir: str | None = None) -> str:
+    """Build librsi.so if any source is newer; return its path.  `extra`
+    adds nvcc flags; `out` / `objdir` / `src_dir` build a variant elsewhere."""
+    lib = out or LIB
+    objs_dir = objdir or BUILD
+    if not force and out is None and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(objs_dir, exist_ok=True)
     cc = nvcc()
-    srcs = _sources()
+    srcs = _sources(src_dir)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, "-c", src, "-o", obj] + ARCH + FLAGS + list(extra)
+        obj = os.path.join(objs_dir, os.path.basename(src)[:-3] + ".o")
+        inc = ["-I" + src_dir] if src_dir else []
+        cmd = [cc, "-c", src, "-o", obj] + ARCH + inc + FLAGS + list(extra)
         if verbose:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -71,13 +76,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if verbose:
         for _, log in results:
             print(log)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc, "-shared", "-o", tmp] + ARCH + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

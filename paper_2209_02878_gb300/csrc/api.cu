@@ -28,7 +28,7 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-constexpr int kDefaultSmemNodes = 511;  // 32 KB of treelet per block
+constexpr int kDefaultBlock = 128;
 
 // Carves the device buffers of a tree over N triangles and M meshes out of
 // one allocation.  With base == nullptr only the total size is computed.
@@ -49,8 +49,10 @@ size_t carve(TreeBufs& tb, int64_t N, int M, int nblk, char* base) {
     tb.vals[0] = (uint32_t*)take(4 * n1);
     tb.vals[1] = (uint32_t*)take(4 * n1);
     tb.hist = (uint32_t*)take(4 * (size_t)rsi::kSortBins * (tb.ntiles > 0 ? tb.ntiles : 1));
+    tb.totals = (uint32_t*)take(4 * (size_t)rsi::kSortBins);
     tb.partial = (float*)take(4 * 6 * (size_t)(nblk > 0 ? nblk : 1));
     tb.bounds = (float*)take(4 * 6 * (size_t)M);
+    tb.rootbox = (float4*)take(16 * 2 * (size_t)M);
     tb.child = (int32_t*)take(4 * 2 * n1);
     tb.range = (int32_t*)take(4 * 2 * n1);
     tb.parent = (int32_t*)take(4 * 2 * n1);
@@ -58,6 +60,7 @@ size_t carve(TreeBufs& tb, int64_t N, int M, int nblk, char* base) {
     tb.nbox = (float4*)take(16 * 2 * n1);
     tb.lbox = (float4*)take(16 * 2 * n1);
     tb.nodes = (float4*)take(16 * 4 * n1);
+    tb.nodes4 = (float4*)take(16 * 8 * n1);
     tb.tris = (float4*)take(16 * 3 * n1);
     tb.treelet = (float4*)take(M == 1 ? 16 * 4 * (size_t)rsi::kTreeletMax : 16);
     tb.treelet_n = (int32_t*)take(4);
@@ -80,14 +83,16 @@ rsi_status check_build_opts(const rsi_build_opts* o, int32_t* leaf, int32_t* lev
 }
 
 struct LaunchCfg {
-    int block, stack, smem_nodes;
+    int block, stack, smem_nodes, sort_bits, width;
     bool stats;
 };
 
 rsi_status check_launch_opts(const rsi_launch_opts* lo, bool has_treelet, LaunchCfg* c) {
-    c->block = 256;
+    c->block = kDefaultBlock;
     c->stack = 64;
     c->smem_nodes = 0;
+    c->sort_bits = 0;
+    c->width = 2;
     c->stats = false;
     int sm = 0;
     if (lo) {
@@ -102,9 +107,15 @@ rsi_status check_launch_opts(const rsi_launch_opts* lo, bool has_treelet, Launch
         }
         if (lo->smem_nodes < -1 || lo->smem_nodes > rsi::kTreeletMax) return RSI_ERR_ARG;
         sm = lo->smem_nodes;
+        if (lo->sort_bits != 0 && lo->sort_bits != -1 && (lo->sort_bits < 6 || lo->sort_bits > 30))
+            return RSI_ERR_ARG;
+        c->sort_bits = lo->sort_bits;
+        if (lo->node_width != 0 && lo->node_width != 2 && lo->node_width != 4) return RSI_ERR_ARG;
+        if (lo->node_width != 0) c->width = lo->node_width;
         c->stats = lo->stats != 0;
     }
-    if (has_treelet && sm != -1) c->smem_nodes = sm == 0 ? kDefaultSmemNodes : sm;
+    if (has_treelet && sm > 0) c->smem_nodes = sm;
+    if (c->smem_nodes > 0) c->width = 2;  // the treelet holds binary nodes
     return RSI_OK;
 }
 
@@ -151,7 +162,41 @@ struct rsi_bvh_s {
     unsigned long long* scratch = nullptr;  // [0] work counter, [1..6] stats
     bool built = false;
     cudaStream_t stream = nullptr;
+    char* seg_mem = nullptr;  // segment-order workspace (grown on demand)
+    rsi::SegOrderWs seg_ws{};
+    cudaStream_t seg_stream = nullptr;
 };
+
+namespace {
+// Grow the segment-order workspace of h to n segments (stream-ordered).
+rsi_status ensure_seg_ws(rsi_bvh h, int64_t n, cudaStream_t s) {
+    if (h->seg_mem && h->seg_ws.cap >= n) return RSI_OK;
+    if (h->seg_mem) {
+        cudaFreeAsync(h->seg_mem, s);
+        h->seg_mem = nullptr;
+    }
+    const int64_t ntiles = (n + rsi::kSortTile - 1) / rsi::kSortTile;
+    const size_t b1 = align256(4 * (size_t)n);
+    const size_t bh = align256(4 * (size_t)rsi::kSortBins * (size_t)(ntiles > 0 ? ntiles : 1));
+    const size_t bytes = 4 * b1 + bh + align256(4 * rsi::kSortBins);
+    cudaError_t e = cudaMallocAsync((void**)&h->seg_mem, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->seg_mem = nullptr;
+        return e == cudaErrorMemoryAllocation ? RSI_ERR_OOM : RSI_ERR_CUDA;
+    }
+    char* p = h->seg_mem;
+    h->seg_ws.keys[0] = (uint32_t*)p;
+    h->seg_ws.keys[1] = (uint32_t*)(p + b1);
+    h->seg_ws.vals[0] = (uint32_t*)(p + 2 * b1);
+    h->seg_ws.vals[1] = (uint32_t*)(p + 3 * b1);
+    h->seg_ws.hist = (uint32_t*)(p + 4 * b1);
+    h->seg_ws.totals = (uint32_t*)(p + 4 * b1 + bh);
+    h->seg_ws.cap = n;
+    h->seg_stream = s;
+    return RSI_OK;
+}
+}  // namespace
 
 extern "C" {
 
@@ -296,6 +341,7 @@ rsi_status rsi_bvh_destroy(rsi_bvh h) {
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != h->device) cudaSetDevice(h->device);
+    if (h->seg_mem) cudaFreeAsync(h->seg_mem, h->seg_stream);
     cudaError_t e = cudaFreeAsync(h->mem, h->stream);
     if (cur != h->device) cudaSetDevice(cur);
     delete h;
@@ -367,18 +413,19 @@ static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, in
     if (!h || nR < 0) return RSI_ERR_ARG;
     if (mode != RSI_MODE_BOOL && mode != RSI_MODE_COUNT && mode != RSI_MODE_NEAREST)
         return RSI_ERR_ARG;
-    rsi_status st = check_output(mode, out);
-    if (st != RSI_OK) return st;
+    if (!out) return RSI_ERR_ARG;
     if (!h->built) return RSI_ERR_NOT_BUILT;
     LaunchCfg c;
-    st = check_launch_opts(lo, h->levels > 0 && h->nT > 0, &c);
+    rsi_status st = check_launch_opts(lo, h->levels > 0 && h->nT > 0, &c);
     if (st != RSI_OK) return st;
     if (force_stats) c.stats = true;
-    if (nR == 0) {
-        if (mode != RSI_MODE_BOOL && out->hit_idx)
+    if (nR == 0) {  // no-op (the output arrays may be empty)
+        if (mode != RSI_MODE_BOOL && out->hit_idx && out->n_hits)
             RSI_CK(cudaMemsetAsync(out->n_hits, 0, 8, (cudaStream_t)s));
         return RSI_OK;
     }
+    st = check_output(mode, out);
+    if (st != RSI_OK) return st;
     if (!dA || !dB) return RSI_ERR_ARG;
     rsi::TraceParams P;
     memset(&P, 0, sizeof(P));
@@ -391,7 +438,9 @@ static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, in
         P.root = ~0;
     else
         P.root = (int)(h->nT - 1);
+    P.root4 = h->nT > 0 ? (int)(h->nT - 1) : rsi::kNoRoot;
     P.nodes = h->tb.nodes;
+    P.nodes4 = h->tb.nodes4;
     P.tris = h->tb.tris;
     P.treelet = h->tb.treelet;
     P.treelet_n = h->tb.treelet_n;
@@ -401,8 +450,16 @@ static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, in
     P.max_visits = (int)h->nT + 2;
     P.status = h->tb.status;
     P.out = trav_out(mode, out);
+    P.order = nullptr;
+    const int bits = c.sort_bits;  // 0 or -1: input order
+    if (bits > 0 && h->nT > 0 && nR < ((int64_t)1 << 31)) {
+        st = ensure_seg_ws(h, nR, (cudaStream_t)s);
+        if (st != RSI_OK) return st;
+        RSI_CK(rsi::segment_order(dA, dB, (int)nR, h->tb.rootbox, bits, h->seg_ws,
+                                  (cudaStream_t)s, &P.order));
+    }
     if (c.stats) RSI_CK(cudaMemsetAsync(P.stats, 0, 6 * 8, (cudaStream_t)s));
-    RSI_CK(rsi::launch_trace(P, mode, c.stack, c.stats, c.block, (cudaStream_t)s));
+    RSI_CK(rsi::launch_trace(P, mode, c.stack, c.stats, c.block, c.width, (cudaStream_t)s));
     return RSI_OK;
 }
 
@@ -432,14 +489,14 @@ rsi_status rsi_intersect_stats(rsi_bvh h, const float* dA, const float* dB, int6
 
 rsi_status rsi_intersect_backward(const float* dV, int64_t nV, const int32_t* dT, int64_t nT,
                                   const float* dA, const float* dB, int64_t nR,
-                                  const int32_t* dTri, const float* dTuv, const float* dGradPoint,
+                                  const int32_t* dTri, const float* dGradPoint,
                                   const float* dGradTuv, float* dGradV, float* dGradA,
                                   float* dGradB, rsi_stream s) {
     if (nV < 0 || nT < 0 || nR < 0) return RSI_ERR_ARG;
     if (nR == 0) return RSI_OK;
-    if (!dA || !dB || !dTri || !dTuv || (nT > 0 && (!dV || !dT))) return RSI_ERR_ARG;
-    RSI_CK(rsi::launch_backward(dV, nV, dT, nT, dA, dB, nR, dTri, dTuv, dGradPoint, dGradTuv,
-                                dGradV, dGradA, dGradB, (cudaStream_t)s));
+    if (!dA || !dB || !dTri || (nT > 0 && (!dV || !dT))) return RSI_ERR_ARG;
+    RSI_CK(rsi::launch_backward(dV, nV, dT, nT, dA, dB, nR, dTri, dGradPoint, dGradTuv, dGradV,
+                                dGradA, dGradB, (cudaStream_t)s));
     return RSI_OK;
 }
 
@@ -456,7 +513,8 @@ struct rsi_batch_s {
     int32_t* d_blkmesh = nullptr;
     rsi::BatchItemDev* d_items = nullptr;
     unsigned long long* work = nullptr;
-    int64_t n_chunks = 0;
+    int64_t n_tiles = 0;
+    rsi::BatchTile* d_tiles = nullptr;
     LaunchCfg cfg;
     int32_t leaf = 1;
     cudaStream_t cap = nullptr;
@@ -510,33 +568,40 @@ rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_bu
     };
     std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost(x) > cost(y); });
     std::vector<rsi::BatchItemDev> dev(n);
-    int64_t chunk = 0;
+    std::vector<rsi::BatchTile> tiles;
     for (int q = 0; q < n; ++q) {
         const int k = ord[q];
         const rsi_batch_item& it = items[k];
-        rsi::BatchItemDev& d = dev[q];
+        rsi::BatchItemDev& d = dev[k];
         d.A = it.dA;
         d.B = it.dB;
         d.nR = it.nR;
         d.root = it.nT > 0 ? (int)(table[k].off + it.nT - 1) : rsi::kNoRoot;
         d.mode = it.mode;
-        d.chunk0 = chunk;
         d.out = trav_out((rsi_mode)it.mode, &it.out);
-        chunk += (it.nR + 31) / 32;
+        for (int64_t lo = 0; lo < it.nR; lo += rsi::kBatchTile) {
+            rsi::BatchTile t;
+            t.item = k;
+            t.pad = 0;
+            t.lo = lo;
+            t.hi = lo + rsi::kBatchTile < it.nR ? lo + rsi::kBatchTile : it.nR;
+            tiles.push_back(t);
+        }
     }
     rsi_batch b = new rsi_batch_s();
     RSI_CK(cudaGetDevice(&b->device));
     b->items.assign(items, items + n);
     b->cfg = cfg;
     b->leaf = leaf;
-    b->n_chunks = chunk;
+    b->n_tiles = (int64_t)tiles.size();
     TreeBufs tb;
     memset(&tb, 0, sizeof(tb));
     const size_t tree_bytes = carve(tb, N, n, nblk, nullptr);
     const size_t tab_bytes = align256(sizeof(MeshDesc) * n);
     const size_t blk_bytes = align256(sizeof(int32_t) * (blkmesh.size() + 1));
     const size_t item_bytes = align256(sizeof(rsi::BatchItemDev) * n);
-    const size_t bytes = tree_bytes + tab_bytes + blk_bytes + item_bytes + 256;
+    const size_t tile_bytes = align256(sizeof(rsi::BatchTile) * (tiles.size() + 1));
+    const size_t bytes = tree_bytes + tab_bytes + blk_bytes + item_bytes + tile_bytes + 256;
     cudaStream_t cs = (cudaStream_t)s;
     cudaError_t e = cudaMallocAsync((void**)&b->mem, bytes, cs);
     if (e != cudaSuccess) {
@@ -552,6 +617,7 @@ rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_bu
     b->d_table = (MeshDesc*)(b->mem + tree_bytes);
     b->d_blkmesh = (int32_t*)(b->mem + tree_bytes + tab_bytes);
     b->d_items = (rsi::BatchItemDev*)(b->mem + tree_bytes + tab_bytes + blk_bytes);
+    b->d_tiles = (rsi::BatchTile*)(b->mem + tree_bytes + tab_bytes + blk_bytes + item_bytes);
     b->work = (unsigned long long*)(b->mem + bytes - 256);
     b->stream = cs;
     e = cudaMemcpyAsync(b->d_table, table.data(), sizeof(MeshDesc) * n, cudaMemcpyHostToDevice, cs);
@@ -560,6 +626,9 @@ rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_bu
                             cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_items, dev.data(), sizeof(rsi::BatchItemDev) * n,
+                            cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && !tiles.empty())
+        e = cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(rsi::BatchTile) * tiles.size(),
                             cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(tb.status, 0, 4, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);  // host tables go out of scope
@@ -602,8 +671,10 @@ rsi_status rsi_batch_intersect(rsi_batch b, rsi_stream s) {
     rsi::BatchParams P;
     P.items = b->d_items;
     P.n_items = (int)b->items.size();
-    P.n_chunks = b->n_chunks;
+    P.tiles = b->d_tiles;
+    P.n_tiles = b->n_tiles;
     P.nodes = b->tb.nodes;
+    P.nodes4 = b->tb.nodes4;
     P.tris = b->tb.tris;
     P.work = b->work;
     P.max_visits = b->tb.N + 2;

@@ -8,7 +8,12 @@
 //     dL/da = (1-t)(gP + lambda),  dL/db = t (gP + lambda),
 //     dL/dv0 = -(1-u-v) lambda, dL/dv1 = -u lambda, dL/dv2 = -v lambda.
 // One thread per segment; vertex gradients are scattered with atomicAdd
-// (the only cross-segment reduction).  FP32.
+// (the only cross-segment reduction).  The per-segment algebra and the
+// vertex accumulation run in FP64 -- (t, u, v) recomputed from the geometry
+// as in the definition -- because a vertex gradient is a sum of a few
+// contributions that can cancel, and FP32 atomics would leave an absolute
+// error proportional to the sum of their magnitudes; the total is rounded
+// to FP32 once.
 #include <cuda_runtime.h>
 
 #include "rsi_trace.h"
@@ -18,79 +23,105 @@ namespace rsi {
 __global__ void k_backward(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ T,
                            int64_t nT, const float* __restrict__ A, const float* __restrict__ B,
                            int64_t nR, const int32_t* __restrict__ tri,
-                           const float* __restrict__ tuv, const float* __restrict__ gP,
-                           const float* __restrict__ gtuv, float* __restrict__ gV,
-                           float* __restrict__ gA, float* __restrict__ gB) {
+                           const float* __restrict__ gP, const float* __restrict__ gtuv,
+                           double* __restrict__ gV64, float* __restrict__ gA,
+                           float* __restrict__ gB) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nR) return;
     const int j = tri[i];
-    float ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
+    double ga[3] = {0.0, 0.0, 0.0}, gb[3] = {0.0, 0.0, 0.0};
     if (j >= 0 && j < nT) {
         const int64_t i0 = T[3 * (int64_t)j], i1 = T[3 * (int64_t)j + 1], i2 = T[3 * (int64_t)j + 2];
         if (i0 >= 0 && i0 < nV && i1 >= 0 && i1 < nV && i2 >= 0 && i2 < nV) {
-            float a[3], d[3], e1[3], e2[3];
+            double d[3], e1[3], e2[3], s0[3], nd[3];
             for (int k = 0; k < 3; ++k) {
-                a[k] = A[3 * i + k];
-                d[k] = B[3 * i + k] - a[k];
-                const float v0 = V[3 * i0 + k];
-                e1[k] = V[3 * i1 + k] - v0;
-                e2[k] = V[3 * i2 + k] - v0;
+                const double a = A[3 * i + k], v0 = V[3 * i0 + k];
+                d[k] = (double)B[3 * i + k] - a;
+                nd[k] = -d[k];
+                e1[k] = (double)V[3 * i1 + k] - v0;
+                e2[k] = (double)V[3 * i2 + k] - v0;
+                s0[k] = a - v0;
             }
-            const float nd[3] = {-d[0], -d[1], -d[2]};
-            const float c12[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
-                                  e1[0] * e2[1] - e1[1] * e2[0]};
-            const float c20[3] = {e2[1] * nd[2] - e2[2] * nd[1], e2[2] * nd[0] - e2[0] * nd[2],
-                                  e2[0] * nd[1] - e2[1] * nd[0]};
-            const float c01[3] = {nd[1] * e1[2] - nd[2] * e1[1], nd[2] * e1[0] - nd[0] * e1[2],
-                                  nd[0] * e1[1] - nd[1] * e1[0]};
-            const float detM = nd[0] * c12[0] + nd[1] * c12[1] + nd[2] * c12[2];
-            if (detM != 0.f) {
-                const float t = tuv[3 * i], u = tuv[3 * i + 1], v = tuv[3 * i + 2];
-                float gp[3] = {0.f, 0.f, 0.f};
+            const double c12[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                   e1[0] * e2[1] - e1[1] * e2[0]};
+            const double c20[3] = {e2[1] * nd[2] - e2[2] * nd[1], e2[2] * nd[0] - e2[0] * nd[2],
+                                   e2[0] * nd[1] - e2[1] * nd[0]};
+            const double c01[3] = {nd[1] * e1[2] - nd[2] * e1[1], nd[2] * e1[0] - nd[0] * e1[2],
+                                   nd[0] * e1[1] - nd[1] * e1[0]};
+            const double detM = nd[0] * c12[0] + nd[1] * c12[1] + nd[2] * c12[2];
+            if (detM != 0.0) {
+                // x = M^-1 (a - v0): the rows of M^-1 are c12, c20, c01 over det M
+                const double inv = 1.0 / detM;
+                const double t = (c12[0] * s0[0] + c12[1] * s0[1] + c12[2] * s0[2]) * inv;
+                const double u = (c20[0] * s0[0] + c20[1] * s0[1] + c20[2] * s0[2]) * inv;
+                const double v = (c01[0] * s0[0] + c01[1] * s0[1] + c01[2] * s0[2]) * inv;
+                double gp[3] = {0.0, 0.0, 0.0};
                 if (gP) {
                     gp[0] = gP[3 * i];
                     gp[1] = gP[3 * i + 1];
                     gp[2] = gP[3 * i + 2];
                 }
-                float gx0 = gp[0] * d[0] + gp[1] * d[1] + gp[2] * d[2];
-                float gx1 = 0.f, gx2 = 0.f;
+                double gx0 = gp[0] * d[0] + gp[1] * d[1] + gp[2] * d[2];
+                double gx1 = 0.0, gx2 = 0.0;
                 if (gtuv) {
                     gx0 += gtuv[3 * i];
                     gx1 = gtuv[3 * i + 1];
                     gx2 = gtuv[3 * i + 2];
                 }
-                const float inv = 1.f / detM;
-                const float w = 1.f - u - v;
+                const double w = 1.0 - u - v;
                 for (int k = 0; k < 3; ++k) {
-                    const float lam = (gx0 * c12[k] + gx1 * c20[k] + gx2 * c01[k]) * inv;
-                    const float s = gp[k] + lam;
-                    ga[k] = (1.f - t) * s;
-                    gb[k] = t * s;
-                    if (gV) {
-                        atomicAdd(gV + 3 * i0 + k, -w * lam);
-                        atomicAdd(gV + 3 * i1 + k, -u * lam);
-                        atomicAdd(gV + 3 * i2 + k, -v * lam);
+                    const double lam = (gx0 * c12[k] + gx1 * c20[k] + gx2 * c01[k]) * inv;
+                    const double sk = gp[k] + lam;
+                    ga[k] = (1.0 - t) * sk;
+                    gb[k] = t * sk;
+                    if (gV64) {
+                        atomicAdd(gV64 + 3 * i0 + k, -w * lam);
+                        atomicAdd(gV64 + 3 * i1 + k, -u * lam);
+                        atomicAdd(gV64 + 3 * i2 + k, -v * lam);
                     }
                 }
             }
         }
     }
     if (gA)
-        for (int k = 0; k < 3; ++k) gA[3 * i + k] = ga[k];
+        for (int k = 0; k < 3; ++k) gA[3 * i + k] = (float)ga[k];
     if (gB)
-        for (int k = 0; k < 3; ++k) gB[3 * i + k] = gb[k];
+        for (int k = 0; k < 3; ++k) gB[3 * i + k] = (float)gb[k];
+}
+
+// dGradV += the FP64 accumulator, rounded once.
+__global__ void k_add_grad(float* __restrict__ gV, const double* __restrict__ gV64, int64_t n) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) gV[k] = (float)((double)gV[k] + gV64[k]);
 }
 
 cudaError_t launch_backward(const float* V, int64_t nV, const int32_t* T, int64_t nT,
                             const float* A, const float* B, int64_t nR, const int32_t* tri,
-                            const float* tuv, const float* gP, const float* gtuv, float* gV,
-                            float* gA, float* gB, cudaStream_t s) {
+                            const float* gP, const float* gtuv, float* gV, float* gA, float* gB,
+                            cudaStream_t s) {
     if (nR == 0) return cudaSuccess;
     const int block = 256;
-    const int64_t grid = (nR + block - 1) / block;
-    k_backward<<<(unsigned)grid, block, 0, s>>>(V, nV, T, nT, A, B, nR, tri, tuv, gP, gtuv, gV,
-                                                gA, gB);
-    return cudaGetLastError();
+    double* acc = nullptr;
+    const size_t bytes = sizeof(double) * 3 * (size_t)(nV > 0 ? nV : 1);
+    cudaError_t e = cudaSuccess;
+    if (gV) {
+        e = cudaMallocAsync((void**)&acc, bytes, s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(acc, 0, bytes, s);
+        if (e != cudaSuccess) return e;
+    }
+    k_backward<<<(unsigned)((nR + block - 1) / block), block, 0, s>>>(V, nV, T, nT, A, B, nR, tri,
+                                                                     gP, gtuv, acc, gA, gB);
+    e = cudaGetLastError();
+    if (gV && e == cudaSuccess && nV > 0) {
+        k_add_grad<<<(unsigned)((3 * nV + block - 1) / block), block, 0, s>>>(gV, acc, 3 * nV);
+        e = cudaGetLastError();
+    }
+    if (acc) {
+        const cudaError_t f = cudaFreeAsync(acc, s);
+        if (e == cudaSuccess) e = f;
+    }
+    return e;
 }
 
 }  // namespace rsi

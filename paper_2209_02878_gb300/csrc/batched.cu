@@ -1,11 +1,11 @@
 // Batched traversal: many independent (mesh, segments, mode) problems in one
-// persistent launch.  The work is a list of 32-segment chunks; items are laid
-// out in decreasing estimated cost per segment (log2 N_t, NEAREST and COUNT
-// weighted above BOOL) so the expensive chunks start first, and each warp
-// pulls the next chunk from one atomic counter, finds its item by binary
-// search over the items' first chunks and runs the same per-segment
-// traversal as the single-mesh kernel in that item's mode.  All meshes live
-// in one concatenated node / triangle storage built by one multi-mesh build.
+// persistent launch.  The work is a list of tiles (up to kBatchTile segments
+// of one item) ordered by decreasing estimated cost per segment (log2 N_t,
+// NEAREST and COUNT weighted above BOOL) so the expensive tiles start first;
+// each warp pulls the next tile from one atomic counter and runs the same
+// per-lane refill traversal as the single-mesh kernel over the tile, in that
+// item's mode.  All meshes live in one concatenated node / triangle storage
+// built by one multi-mesh build.
 #include <cuda_runtime.h>
 
 #include "rsi_trace.h"
@@ -15,40 +15,40 @@ namespace rsi {
 template <int STACK>
 __global__ void k_batch(BatchParams P) {
     TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull};
+    unsigned long long segs = 0;
     const int lane = threadIdx.x & 31;
     while (true) {
-        unsigned long long c = 0ull;
-        if (lane == 0) c = atomicAdd(P.work, 1ull);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= (unsigned long long)P.n_chunks) break;
-        int lo = 0, hi = P.n_items - 1;  // last item with chunk0 <= c
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if ((unsigned long long)P.items[mid].chunk0 <= c)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        const BatchItemDev& it = P.items[lo];
-        const int64_t i = ((int64_t)c - it.chunk0) * 32 + lane;
+        unsigned long long t = 0ull;
+        if (lane == 0) t = atomicAdd(P.work, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (unsigned long long)P.n_tiles) break;
+        const BatchTile tile = P.tiles[t];
+        const BatchItemDev& it = P.items[tile.item];
+        TraceCtx C;
+        C.A = it.A;
+        C.B = it.B;
+        C.nR = it.nR;
+        C.root = it.root;
+        C.root4 = it.root;
+        C.nodes = P.nodes;
+        C.nodes4 = P.nodes4;
+        C.tris = P.tris;
+        C.treelet = nullptr;
+        C.snodes = nullptr;
+        C.S = 0;
+        C.max_visits = P.max_visits;
+        C.order = nullptr;
+        C.status = P.status;
+        C.out = it.out;
         switch (it.mode) {
             case RSI_MODE_BOOL:
-                process_segment<RSI_MODE_BOOL, STACK, false>(it.A, it.B, it.nR, i, it.root,
-                                                             P.nodes, P.tris, nullptr, nullptr,
-                                                             0, P.max_visits, P.status,
-                                                             it.out, st);
+                trace_loop<RSI_MODE_BOOL, STACK, false, 2>(C, nullptr, tile.lo, tile.hi, st, segs);
                 break;
             case RSI_MODE_COUNT:
-                process_segment<RSI_MODE_COUNT, STACK, false>(it.A, it.B, it.nR, i, it.root,
-                                                              P.nodes, P.tris, nullptr, nullptr,
-                                                              0, P.max_visits, P.status,
-                                                              it.out, st);
+                trace_loop<RSI_MODE_COUNT, STACK, false, 2>(C, nullptr, tile.lo, tile.hi, st, segs);
                 break;
             default:
-                process_segment<RSI_MODE_NEAREST, STACK, false>(it.A, it.B, it.nR, i, it.root,
-                                                                P.nodes, P.tris, nullptr,
-                                                                nullptr, 0, P.max_visits,
-                                                                P.status, it.out, st);
+                trace_loop<RSI_MODE_NEAREST, STACK, false, 2>(C, nullptr, tile.lo, tile.hi, st, segs);
                 break;
         }
     }
@@ -69,12 +69,13 @@ const void* batch_kernel(int stack) {
 }
 
 cudaError_t launch_batch(const BatchParams& P, int block, int stack, cudaStream_t s) {
-    if (P.n_chunks == 0) return cudaSuccess;
+    if (P.n_tiles == 0) return cudaSuccess;
     const void* fn = batch_kernel(stack);
+    block = max_block(fn, block);
     int grid = 0;
     cudaError_t e = occupancy_grid(fn, block, 0, &grid);
     if (e != cudaSuccess) return e;
-    const int64_t blocks_needed = (P.n_chunks + block / 32 - 1) / (block / 32);
+    const int64_t blocks_needed = (P.n_tiles + block / 32 - 1) / (block / 32);
     if (blocks_needed < grid) grid = (int)blocks_needed;
     e = cudaMemsetAsync(P.work, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;

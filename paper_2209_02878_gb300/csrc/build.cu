@@ -23,6 +23,7 @@
 
 #include "rsi_build.h"
 #include "rsi_internal.cuh"
+#include "sort.cuh"
 
 namespace rsi {
 
@@ -157,99 +158,6 @@ __global__ void __launch_bounds__(kBuildThreads) k_morton(MeshArgs ma, TreeBufs 
     }
 }
 
-// ---------------------------------------------------------------- a3 sort
-__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t* __restrict__ keys,
-                                                            int n, int shift,
-                                                            uint32_t* __restrict__ hist,
-                                                            int ntiles) {
-    __shared__ uint32_t h[kSortBins];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const int base = blockIdx.x * kSortTile;
-#pragma unroll 4
-    for (int it = 0; it < kSortItems; ++it) {
-        const int pos = base + it * kSortThreads + threadIdx.x;
-        if (pos < n) atomicAdd(&h[(uint32_t)(keys[pos] >> shift) & 0xffu], 1u);
-    }
-    __syncthreads();
-    hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
-}
-
-// Exclusive scan of hist[0..len) in place by one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* hist, int len) {
-    __shared__ uint32_t part[1024];
-    const int per = (len + 1023) / 1024;
-    const int b = threadIdx.x * per, e = min(len, b + per);
-    uint32_t s = 0;
-    for (int q = b; q < e; ++q) s += hist[q];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const uint32_t x = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += x;
-        __syncthreads();
-    }
-    uint32_t run = part[threadIdx.x] - s;
-    for (int q = b; q < e; ++q) {
-        const uint32_t x = hist[q];
-        hist[q] = run;
-        run += x;
-    }
-}
-
-// Stable scatter: each warp owns a contiguous run of 32 * kSortItems keys and
-// ranks equal digits with __match_any_sync in key order; warp counters are
-// then scanned across warps per digit and offset by the global prefix.
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
-    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, int n, int shift, const uint32_t* __restrict__ hist, int ntiles) {
-    constexpr int W = kSortThreads / 32;
-    __shared__ uint32_t cnt[W][kSortBins];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int q = threadIdx.x; q < W * kSortBins; q += kSortThreads) (&cnt[0][0])[q] = 0;
-    __syncthreads();
-    const int wbase = blockIdx.x * kSortTile + w * (32 * kSortItems);
-    const uint32_t lt = (1u << lane) - 1u;
-    uint32_t local[kSortItems];
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-        const int pos = wbase + it * 32 + lane;
-        const bool valid = pos < n;
-        const uint32_t d = valid ? ((uint32_t)(kin[pos] >> shift) & 0xffu) : 0x100u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt);
-        const uint32_t c = valid ? cnt[w][d] : 0u;
-        __syncwarp();
-        if (valid && rank == 0) cnt[w][d] = c + __popc(peers);
-        __syncwarp();
-        local[it] = c + rank;
-    }
-    __syncthreads();
-    {
-        const int d = threadIdx.x;  // kSortThreads == kSortBins
-        uint32_t run = hist[d * ntiles + blockIdx.x];
-#pragma unroll
-        for (int q = 0; q < W; ++q) {
-            const uint32_t x = cnt[q][d];
-            cnt[q][d] = run;
-            run += x;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-        const int pos = wbase + it * 32 + lane;
-        if (pos < n) {
-            const uint64_t k = kin[pos];
-            const uint32_t d = (uint32_t)(k >> shift) & 0xffu;
-            const uint32_t o = cnt[w][d] + local[it];
-            kout[o] = k;
-            vout[o] = vin[pos];
-        }
-    }
-}
-
 // ---------------------------------------------------------------- a4
 // Length of the common prefix of K_i = code_i << 32 | i and K_j (local
 // indices of one mesh); -1 outside [0, n).
@@ -341,6 +249,59 @@ __device__ __forceinline__ void write_root(float4* nodes, int slot, float4 lo, f
     write_node(nodes, slot, lo, hi, ref, cnt, e, e, -1, 0);
 }
 
+// 4-wide traversal node of slot `slot` (8 x float4 = 128 B, one record per
+// binary slot): the grandchildren of the binary node, i.e. each internal
+// child is replaced by its own two children, a leaf child is kept.  Layout:
+// {lo.x[4]}, {lo.y[4]}, {lo.z[4]}, {hi.x[4]}, {hi.y[4]}, {hi.z[4]},
+// {ref[4]}, {cnt[4]}; an empty slot has lo = hi = +inf, ref -1, cnt 0.
+struct Slot4 {
+    float lo[3], hi[3];
+    int ref, cnt;
+};
+
+__device__ __forceinline__ void binary_children(const float4* __restrict__ nodes, int slot,
+                                                Slot4& a, Slot4& b) {
+    const float4* p = nodes + 4 * (int64_t)slot;
+    const float4 f0 = __ldcg(p), f1 = __ldcg(p + 1), f2 = __ldcg(p + 2), f3 = __ldcg(p + 3);
+    a.lo[0] = f0.x; a.lo[1] = f0.y; a.lo[2] = f0.z;
+    a.hi[0] = f0.w; a.hi[1] = f1.x; a.hi[2] = f1.y;
+    b.lo[0] = f1.z; b.lo[1] = f1.w; b.lo[2] = f2.x;
+    b.hi[0] = f2.y; b.hi[1] = f2.z; b.hi[2] = f2.w;
+    a.ref = f2i(f3.x);
+    b.ref = f2i(f3.y);
+    a.cnt = f2i(f3.z);
+    b.cnt = f2i(f3.w);
+}
+
+// Expand binary slot `slot` (whose own record is already written) into its
+// 4-wide record.
+__device__ __forceinline__ void write_node4(const float4* __restrict__ nodes, float4* nodes4,
+                                            int slot) {
+    Slot4 c[2], o[4];
+    binary_children(nodes, slot, c[0], c[1]);
+    int k = 0;
+    for (int q = 0; q < 2; ++q) {
+        if (c[q].cnt == 0 && c[q].ref >= 0) {  // internal: take its two children
+            binary_children(nodes, c[q].ref, o[k], o[k + 1]);
+            k += 2;
+        } else if (c[q].cnt > 0) {
+            o[k++] = c[q];
+        }
+    }
+    for (; k < 4; ++k) {
+        for (int a = 0; a < 3; ++a) o[k].lo[a] = o[k].hi[a] = INFINITY;
+        o[k].ref = -1;
+        o[k].cnt = 0;
+    }
+    float4* d = nodes4 + 8 * (int64_t)slot;
+    for (int a = 0; a < 3; ++a) {
+        __stcg(d + a, make_float4(o[0].lo[a], o[1].lo[a], o[2].lo[a], o[3].lo[a]));
+        __stcg(d + 3 + a, make_float4(o[0].hi[a], o[1].hi[a], o[2].hi[a], o[3].hi[a]));
+    }
+    __stcg(d + 6, make_float4(i2f(o[0].ref), i2f(o[1].ref), i2f(o[2].ref), i2f(o[3].ref)));
+    __stcg(d + 7, make_float4(i2f(o[0].cnt), i2f(o[1].cnt), i2f(o[2].cnt), i2f(o[3].cnt)));
+}
+
 __global__ void k_climb(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ keys,
                         const uint32_t* __restrict__ vals) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -367,8 +328,12 @@ __global__ void k_climb(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ k
     }
     __stcg(tb.lbox + 2 * (int64_t)g, lo);
     __stcg(tb.lbox + 2 * (int64_t)g + 1, hi);
+    const int m = (int)(keys[g] >> 32);
     if (n == 1) {
         write_root(tb.nodes, root_slot, lo, hi, g, 1);
+        write_node4(tb.nodes, tb.nodes4, root_slot);
+        tb.rootbox[2 * m] = lo;
+        tb.rootbox[2 * m + 1] = hi;
         return;
     }
     int node = tb.parent[N + g];
@@ -414,11 +379,15 @@ __global__ void k_climb(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ k
         __stcg(tb.nbox + 2 * (int64_t)node, ulo);
         __stcg(tb.nbox + 2 * (int64_t)node + 1, uhi);
         write_node(tb.nodes, node, cl[0], chh[0], ref[0], cnt[0], cl[1], chh[1], ref[1], cnt[1]);
+        write_node4(tb.nodes, tb.nodes4, node);
         if (node == off) {  // Karras root: fill the root slot
+            tb.rootbox[2 * m] = ulo;
+            tb.rootbox[2 * m + 1] = uhi;
             if (n <= L)
                 write_root(tb.nodes, root_slot, ulo, uhi, off, n);
             else
                 write_root(tb.nodes, root_slot, ulo, uhi, off, 0);
+            write_node4(tb.nodes, tb.nodes4, root_slot);
             return;
         }
         node = tb.parent[node];
@@ -528,20 +497,14 @@ cudaError_t build_tree(TreeBufs& tb, const MeshArgs& ma, cudaStream_t s, bool re
     if (!refit) {
         k_bounds<<<tb.nblk, kBuildThreads, 0, s>>>(ma, tb);
         k_morton<<<tb.nblk, kBuildThreads, 0, s>>>(ma, tb);
-        int cur = 0;
         int shifts[8], np = 0;
         for (int sh = 0; sh < 32; sh += 8) shifts[np++] = sh;
         for (int sh = 32; sh < 64 && ((int64_t)(tb.M - 1) >> (sh - 32)) > 0; sh += 8)
             shifts[np++] = sh;
-        for (int p = 0; p < np; ++p) {
-            k_sort_hist<<<tb.ntiles, kSortThreads, 0, s>>>(tb.keys[cur], N, shifts[p], tb.hist,
-                                                           tb.ntiles);
-            k_sort_scan<<<1, 1024, 0, s>>>(tb.hist, kSortBins * tb.ntiles);
-            k_sort_scatter<<<tb.ntiles, kSortThreads, 0, s>>>(tb.keys[cur], tb.vals[cur],
-                                                              tb.keys[1 - cur], tb.vals[1 - cur],
-                                                              N, shifts[p], tb.hist, tb.ntiles);
-            cur = 1 - cur;
-        }
+        int cur = 0;
+        cudaError_t e = radix_sort<uint64_t>(tb.keys, tb.vals, N, shifts, np, tb.hist, tb.totals,
+                                             s, &cur);
+        if (e != cudaSuccess) return e;
         tb.sorted = cur;
         k_karras<<<cdiv(N, 256), 256, 0, s>>>(ma, tb, tb.keys[cur]);
     } else {
@@ -557,7 +520,7 @@ int build_launches(const TreeBufs& tb, bool refit) {
     if (tb.N == 0) return 0;
     int np = 4;
     for (int sh = 32; sh < 64 && ((int64_t)(tb.M - 1) >> (sh - 32)) > 0; sh += 8) ++np;
-    int k = refit ? 1 : (2 + 3 * np + 1);
+    int k = refit ? 1 : (2 + 3 * np + 1);  // bounds, Morton, np x (hist, scan, scatter), Karras
     k += 1;  // climb
     if (tb.M == 1 && tb.top_levels > 0) k += 1;
     return k;

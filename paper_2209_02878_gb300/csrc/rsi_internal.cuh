@@ -20,6 +20,11 @@
 //                    Slot off+n-1 is the root slot (the paper keeps its root
 //                    pointer in internalNodes[N_t-1] the same way, Sec. 3.1):
 //                    child0 = the Karras root, child1 = empty.
+//   nodes4[8N]       4-wide traversal node per slot = 8 x float4 = 128 B: the
+//                    slot's grandchildren (a leaf child kept as is), SoA:
+//                    {lo.x[4]} {lo.y[4]} {lo.z[4]} {hi.x[4]} {hi.y[4]}
+//                    {hi.z[4]} {ref[4]} {cnt[4]}; traversal over these visits
+//                    every other level of the binary tree
 //   tris[3N]         triangles in leaf order: {v0, orig id}, {v1, -}, {v2, -}
 //   treelet[4 S]     breadth-first copy of the top of one mesh's tree
 #pragma once
@@ -75,10 +80,12 @@ struct TreeBufs {
     uint64_t* keys[2];
     uint32_t* vals[2];
     uint32_t* hist;
+    uint32_t* totals;  // kSortBins digit totals of the current sort pass
     int32_t ntiles;
     int32_t nblk;     // blocks of the bounds / Morton grid
     float* partial;   // 6 * nblk
     float* bounds;    // 6 * M
+    float4* rootbox;  // 2 * M: box of each mesh (lo, hi)
     int32_t* child;   // 2N
     int32_t* range;   // 2N
     int32_t* parent;  // 2N
@@ -86,6 +93,7 @@ struct TreeBufs {
     float4* nbox;     // 2N
     float4* lbox;     // 2N
     float4* nodes;    // 4N
+    float4* nodes4;   // 8N: 4-wide records (grandchildren of each slot)
     float4* tris;     // 3N
     float4* treelet;  // 4 * kTreeletMax (single-mesh trees)
     int32_t* treelet_n;
@@ -282,6 +290,83 @@ static __device__ __noinline__ int mt64(float ax_, float ay_, float az_, float b
         tuv[2] = __ddiv_rn(nv, det);
     }
     return hit;
+}
+
+// ---------------------------------------------------------------- double-float
+// Unevaluated sums h + l of two floats (about 44 significant bits) built from
+// the error-free transformations two-sum (Knuth) and two-product (via FMA),
+// for the nearest hit's (t, u, v): FP64 is one to two orders of magnitude
+// slower than FP32 on this GPU, and these values need more than FP32 only
+// when the segment meets the triangle at a grazing angle.
+struct dfl {
+    float h, l;
+};
+
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ dfl df_fast(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    dfl s = df_two_sum(a.h, b.h);
+    const float e = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+    return df_fast(s.h, e);
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+    return df_fast(p, e);
+}
+
+__device__ __forceinline__ dfl df_div(dfl a, dfl b) {
+    const float q1 = __fdiv_rn(a.h, b.h);
+    const dfl r = df_add(a, df_neg(df_mul(b, {q1, 0.f})));
+    const float q2 = __fdiv_rn(r.h, b.h);
+    return df_fast(q1, q2);
+}
+
+__device__ __forceinline__ float df_float(dfl a) { return __fadd_rn(a.h, a.l); }
+
+// (t, u, v) of the segment a -> b against triangle (v0, v1, v2) in
+// double-float, in the operation order of the definition (differences are
+// exact in double-float).  Only used for values, never for decisions.
+static __device__ __noinline__ void mt_df(const float* a3, const float* b3, float4 A, float4 B,
+                                   float4 C, float* tuv) {
+    dfl d[3], e1[3], e2[3], s0[3];
+    const float v0[3] = {A.x, A.y, A.z}, v1[3] = {B.x, B.y, B.z}, v2[3] = {C.x, C.y, C.z};
+    for (int k = 0; k < 3; ++k) {
+        d[k] = df_two_sum(b3[k], -a3[k]);
+        e1[k] = df_two_sum(v1[k], -v0[k]);
+        e2[k] = df_two_sum(v2[k], -v0[k]);
+        s0[k] = df_two_sum(a3[k], -v0[k]);
+    }
+    auto cross = [](const dfl* x, const dfl* y, dfl* r) {
+        r[0] = df_add(df_mul(x[1], y[2]), df_neg(df_mul(x[2], y[1])));
+        r[1] = df_add(df_mul(x[2], y[0]), df_neg(df_mul(x[0], y[2])));
+        r[2] = df_add(df_mul(x[0], y[1]), df_neg(df_mul(x[1], y[0])));
+    };
+    auto dot = [](const dfl* x, const dfl* y) {
+        return df_add(df_add(df_mul(x[0], y[0]), df_mul(x[1], y[1])), df_mul(x[2], y[2]));
+    };
+    dfl p[3], q[3];
+    cross(d, e2, p);
+    const dfl det = dot(e1, p);
+    cross(s0, e1, q);
+    const dfl nu = dot(s0, p), nv = dot(d, q), nt = dot(e2, q);
+    tuv[0] = df_float(df_div(nt, det));
+    tuv[1] = df_float(df_div(nu, det));
+    tuv[2] = df_float(df_div(nv, det));
 }
 
 }  // namespace rsi

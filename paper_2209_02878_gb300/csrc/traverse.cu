@@ -12,7 +12,7 @@
 
 namespace rsi {
 
-template <int MODE, int STACK, bool STATS>
+template <int MODE, int STACK, bool STATS, int W>
 __global__ void k_trace(TraceParams P) {
     extern __shared__ float4 snodes[];
     int S = 0;
@@ -21,42 +21,49 @@ __global__ void k_trace(TraceParams P) {
         for (int q = threadIdx.x; q < 4 * S; q += blockDim.x) snodes[q] = P.treelet[q];
         __syncthreads();
     }
+    TraceCtx C;
+    C.A = P.A;
+    C.B = P.B;
+    C.nR = P.nR;
+    C.root = P.root;
+    C.root4 = P.root4;
+    C.nodes = P.nodes;
+    C.nodes4 = P.nodes4;
+    C.tris = P.tris;
+    C.treelet = P.treelet;
+    C.snodes = snodes;
+    C.S = S;
+    C.max_visits = P.max_visits;
+    C.order = P.order;
+    C.status = P.status;
+    C.out = P.out;
     TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull};
     unsigned long long segs = 0;
-    const int lane = threadIdx.x & 31;
-    while (true) {
-        unsigned long long base = 0ull;
-        if (lane == 0) base = atomicAdd(P.work, 32ull);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= (unsigned long long)P.nR) break;
-        const int64_t i = (int64_t)base + lane;
-        if (STATS && i < P.nR) ++segs;
-        process_segment<MODE, STACK, STATS>(P.A, P.B, P.nR, i, P.root, P.nodes, P.tris, P.treelet,
-                                            snodes, S, P.max_visits, P.status, P.out, st);
-    }
+    trace_loop<MODE, STACK, STATS, W>(C, P.work, 0, P.nR, st, segs);
     if (STATS) flush_stats(st, P.stats, segs);
 }
 
 using KernelFn = void (*)(TraceParams);
 
-template <int MODE, bool STATS>
+template <int MODE, bool STATS, int W>
 static KernelFn pick_stack(int stack) {
     switch (stack) {
-        case 16: return k_trace<MODE, 16, STATS>;
-        case 32: return k_trace<MODE, 32, STATS>;
-        default: return k_trace<MODE, 64, STATS>;
+        case 16: return k_trace<MODE, 16, STATS, W>;
+        case 32: return k_trace<MODE, 32, STATS, W>;
+        default: return k_trace<MODE, 64, STATS, W>;
     }
 }
 
-KernelFn trace_kernel(int mode, int stack, bool stats) {
-    if (stats) {
-        if (mode == RSI_MODE_BOOL) return pick_stack<RSI_MODE_BOOL, true>(stack);
-        if (mode == RSI_MODE_COUNT) return pick_stack<RSI_MODE_COUNT, true>(stack);
-        return pick_stack<RSI_MODE_NEAREST, true>(stack);
-    }
-    if (mode == RSI_MODE_BOOL) return pick_stack<RSI_MODE_BOOL, false>(stack);
-    if (mode == RSI_MODE_COUNT) return pick_stack<RSI_MODE_COUNT, false>(stack);
-    return pick_stack<RSI_MODE_NEAREST, false>(stack);
+template <bool STATS, int W>
+static KernelFn pick_mode(int mode, int stack) {
+    if (mode == RSI_MODE_BOOL) return pick_stack<RSI_MODE_BOOL, STATS, W>(stack);
+    if (mode == RSI_MODE_COUNT) return pick_stack<RSI_MODE_COUNT, STATS, W>(stack);
+    return pick_stack<RSI_MODE_NEAREST, STATS, W>(stack);
+}
+
+KernelFn trace_kernel(int mode, int stack, bool stats, int width) {
+    if (width == 2) return stats ? pick_mode<true, 2>(mode, stack) : pick_mode<false, 2>(mode, stack);
+    return stats ? pick_mode<true, 4>(mode, stack) : pick_mode<false, 4>(mode, stack);
 }
 
 struct OccKey {
@@ -111,14 +118,22 @@ cudaError_t occupancy_grid(const void* fn, int block, int smem, int* grid) {
     return cudaSuccess;
 }
 
+int max_block(const void* fn, int block) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return block;
+    const int cap = (fa.maxThreadsPerBlock / 32) * 32;
+    return block > cap ? cap : block;
+}
+
 cudaError_t launch_trace(const TraceParams& P, int mode, int stack, bool stats, int block,
-                         cudaStream_t s) {
-    KernelFn fn = trace_kernel(mode, stack, stats);
+                         int width, cudaStream_t s) {
+    KernelFn fn = trace_kernel(mode, stack, stats, width);
+    block = max_block((const void*)fn, block);  // register-limited kernels cap the block
     const int smem = P.smem_nodes > 0 ? P.smem_nodes * 64 : 0;
     int grid = 0;
     cudaError_t e = occupancy_grid((const void*)fn, block, smem, &grid);
     if (e != cudaSuccess) return e;
-    const int64_t warps_needed = (P.nR + 31) / 32;
+    const int64_t warps_needed = (P.nR + kFetchChunk - 1) / kFetchChunk;
     const int64_t blocks_needed = (warps_needed + block / 32 - 1) / (block / 32);
     if (blocks_needed < grid) grid = (int)blocks_needed;
     if (grid < 1) grid = 1;

@@ -126,90 +126,184 @@ __device__ __forceinline__ bool leaf_test(const Seg& s, const float* A, const fl
     return false;
 }
 
-// Returns false when the stack overflowed (result incomplete).
+// Everything one traversal launch needs (by value in registers / params).
+struct TraceCtx {
+    const float* A;
+    const float* B;
+    int64_t nR;
+    int root;   // treelet node ~0, a global root slot, or kNoRoot
+    int root4;  // root slot for 4-wide traversal
+    const float4* nodes;
+    const float4* nodes4;  // 4-wide records (see rsi_internal.cuh)
+    const float4* tris;
+    const float4* treelet;
+    const float4* snodes;  // shared-memory copy of treelet[0..S)
+    int S;
+    int max_visits;
+    const int32_t* order;  // optional processing order of the segments
+    int32_t* status;
+    TravOut out;
+};
+
+// One node visit of segment i: test both child boxes, test the triangles of
+// child leaves, then descend (near child first, far child pushed) or pop.
+// Returns true when the segment is finished (stack empty, a BOOL crossing,
+// a stack overflow, or the visit bound).
 template <int MODE, int STACK, bool STATS>
-__device__ __forceinline__ bool trace(const Seg& s, const float* A, const float* B, int64_t i,
-                                      int root, const float4* __restrict__ nodes,
-                                      const float4* __restrict__ tris,
-                                      const float4* __restrict__ treelet, const float4* snodes,
-                                      int S, int max_visits, int32_t* status, Result& res,
-                                      TravStats& st) {
-    int stack[STACK];
-    int sp = 0;
-    int node = root;
-    float tlim = 1.f;
-    // each node of a tree is visited at most once per segment
-    for (int visits = 0;; ++visits) {
-        if (visits > max_visits) {
-            atomicCAS(status, 0, RSI_ERR_INTERNAL);
-            break;
-        }
-        float4 n0, n1, n2, n3;
-        if (node < 0) {
-            const int k = ~node;
-            if (k < S) {
-                n0 = snodes[4 * k];
-                n1 = snodes[4 * k + 1];
-                n2 = snodes[4 * k + 2];
-                n3 = snodes[4 * k + 3];
-            } else {
-                const float4* p = treelet + 4 * (int64_t)k;
-                n0 = ld4(p);
-                n1 = ld4(p + 1);
-                n2 = ld4(p + 2);
-                n3 = ld4(p + 3);
-            }
+__device__ __forceinline__ bool node_step(const TraceCtx& C, const Seg& s, int64_t i, int& node,
+                                          int& sp, int* stack, float& tlim, Result& res,
+                                          int& visits, bool& overflow, TravStats& st) {
+    if (++visits > C.max_visits) {
+        atomicCAS(C.status, 0, RSI_ERR_INTERNAL);
+        return true;
+    }
+    float4 n0, n1, n2, n3;
+    if (node < 0) {
+        const int k = ~node;
+        if (k < C.S) {
+            n0 = C.snodes[4 * k];
+            n1 = C.snodes[4 * k + 1];
+            n2 = C.snodes[4 * k + 2];
+            n3 = C.snodes[4 * k + 3];
         } else {
-            const float4* p = nodes + 4 * (int64_t)node;
+            const float4* p = C.treelet + 4 * (int64_t)k;
             n0 = ld4(p);
             n1 = ld4(p + 1);
             n2 = ld4(p + 2);
             n3 = ld4(p + 3);
         }
-        if (STATS) ++st.visits;
-        float t0, t1;
-        const bool h0 = slab(s, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, tlim, t0);
-        const bool h1 = slab(s, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, tlim, t1);
-        const int r0 = f2i(n3.x), r1 = f2i(n3.y), c0 = f2i(n3.z), c1 = f2i(n3.w);
-        if (h0 && c0 > 0) {
-            if (leaf_test<MODE, STATS>(s, A, B, i, tris, r0, c0, res, tlim, st)) return true;
-        }
-        if (h1 && c1 > 0) {
-            if (leaf_test<MODE, STATS>(s, A, B, i, tris, r1, c1, res, tlim, st)) return true;
-        }
-        const bool g0 = h0 && c0 <= 0, g1 = h1 && c1 <= 0;
-        const int x0 = c0 < 0 ? ~r0 : r0, x1 = c1 < 0 ? ~r1 : r1;
-        if (g0 && g1) {
-            const bool near0 = t0 <= t1;
-            if (sp >= STACK) return false;
-            stack[sp++] = near0 ? x1 : x0;
-            node = near0 ? x0 : x1;
-        } else if (g0) {
-            node = x0;
-        } else if (g1) {
-            node = x1;
-        } else {
-            if (sp == 0) break;
-            node = stack[--sp];
-        }
+    } else {
+        const float4* p = C.nodes + 4 * (int64_t)node;
+        n0 = ld4(p);
+        n1 = ld4(p + 1);
+        n2 = ld4(p + 2);
+        n3 = ld4(p + 3);
     }
-    return true;
+    if (STATS) ++st.visits;
+    float t0, t1;
+    const bool h0 = slab(s, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, tlim, t0);
+    const bool h1 = slab(s, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, tlim, t1);
+    const int r0 = f2i(n3.x), r1 = f2i(n3.y), c0 = f2i(n3.z), c1 = f2i(n3.w);
+    if (h0 && c0 > 0 && leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r0, c0, res, tlim, st))
+        return true;
+    if (h1 && c1 > 0 && leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r1, c1, res, tlim, st))
+        return true;
+    const bool g0 = h0 && c0 <= 0, g1 = h1 && c1 <= 0;
+    const int x0 = c0 < 0 ? ~r0 : r0, x1 = c1 < 0 ? ~r1 : r1;
+    if (g0 && g1) {
+        if (sp >= STACK) {
+            overflow = true;
+            return true;
+        }
+        const bool near0 = t0 <= t1;
+        stack[sp++] = near0 ? x1 : x0;
+        node = near0 ? x0 : x1;
+    } else if (g0) {
+        node = x0;
+    } else if (g1) {
+        node = x1;
+    } else {
+        if (sp == 0) return true;
+        node = stack[--sp];
+    }
+    return false;
+}
+
+// Compare-exchange of (key, value) pairs, ascending by key.
+__device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb) {
+    const bool sw = kb < ka;
+    const float k = sw ? kb : ka;
+    kb = sw ? ka : kb;
+    ka = k;
+    const int v = sw ? vb : va;
+    vb = sw ? va : vb;
+    va = v;
+}
+
+// One visit of a 4-wide node (the grandchildren of binary slot `node`):
+// test the four child boxes, test the triangles of child leaves, continue
+// with the nearest internal child and push the others farthest first.
+// Returns true when the segment is finished.
+template <int MODE, int STACK, bool STATS>
+__device__ __forceinline__ bool node_step4(const TraceCtx& C, const Seg& s, int64_t i, int& node,
+                                           int& sp, int* stack, float& tlim, Result& res,
+                                           int& visits, bool& overflow, TravStats& st) {
+    if (++visits > C.max_visits) {
+        atomicCAS(C.status, 0, RSI_ERR_INTERNAL);
+        return true;
+    }
+    const float4* p = C.nodes4 + 8 * (int64_t)node;
+    const float4 lx = ld4(p), ly = ld4(p + 1), lz = ld4(p + 2);
+    const float4 hx = ld4(p + 3), hy = ld4(p + 4), hz = ld4(p + 5);
+    const float4 rf = ld4(p + 6), ct = ld4(p + 7);
+    if (STATS) ++st.visits;
+    const int r[4] = {f2i(rf.x), f2i(rf.y), f2i(rf.z), f2i(rf.w)};
+    const int c[4] = {f2i(ct.x), f2i(ct.y), f2i(ct.z), f2i(ct.w)};
+    float t[4];
+    bool h[4];
+    h[0] = slab(s, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, tlim, t[0]);
+    h[1] = slab(s, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, tlim, t[1]);
+    h[2] = slab(s, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, tlim, t[2]);
+    h[3] = slab(s, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, tlim, t[3]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (h[q] && c[q] > 0 &&
+            leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r[q], c[q], res, tlim, st))
+            return true;
+    // internal children, sorted by entry parameter (misses keyed +inf)
+    float k0 = (h[0] && c[0] == 0) ? t[0] : INFINITY, k1 = (h[1] && c[1] == 0) ? t[1] : INFINITY;
+    float k2 = (h[2] && c[2] == 0) ? t[2] : INFINITY, k3 = (h[3] && c[3] == 0) ? t[3] : INFINITY;
+    int v0 = r[0], v1 = r[1], v2 = r[2], v3 = r[3];
+    const int n_int = (k0 < INFINITY) + (k1 < INFINITY) + (k2 < INFINITY) + (k3 < INFINITY);
+    if (n_int == 0) {
+        if (sp == 0) return true;
+        node = stack[--sp];
+        return false;
+    }
+    if (n_int > 1) {
+        cswap(k0, v0, k1, v1);
+        cswap(k2, v2, k3, v3);
+        cswap(k0, v0, k2, v2);
+        cswap(k1, v1, k3, v3);
+        cswap(k1, v1, k2, v2);
+        if (sp + n_int - 1 > STACK) {
+            overflow = true;
+            return true;
+        }
+        if (n_int > 3) stack[sp++] = v3;
+        if (n_int > 2) stack[sp++] = v2;
+        stack[sp++] = v1;
+    } else {
+        // the single internal child: move it to slot 0
+        v0 = k0 < INFINITY ? v0 : k1 < INFINITY ? v1 : k2 < INFINITY ? v2 : v3;
+    }
+    node = v0;
+    return false;
+}
+
+// Whole traversal of one segment (used for the deep-stack re-run).
+// Returns false when the stack overflowed (result incomplete).
+template <int MODE, int STACK, bool STATS>
+__device__ __forceinline__ bool trace(const TraceCtx& C, const Seg& s, int64_t i, Result& res,
+                                      TravStats& st) {
+    int stack[STACK];
+    int sp = 0, node = C.root, visits = 0;
+    float tlim = 1.f;
+    bool overflow = false;
+    while (!node_step<MODE, STACK, STATS>(C, s, i, node, sp, stack, tlim, res, visits, overflow, st)) {
+    }
+    return !overflow;
 }
 
 // Deep-stack re-run for segments whose stack overflowed (a radix tree over
 // 62-bit keys is at most 63 levels deep, so 64 entries always suffice).
 template <int MODE, bool STATS>
-__device__ __noinline__ void trace_deep(const Seg& s, const float* A, const float* B, int64_t i,
-                                        int root, const float4* __restrict__ nodes,
-                                        const float4* __restrict__ tris,
-                                        const float4* __restrict__ treelet, const float4* snodes,
-                                        int S, int max_visits, int32_t* status, Result& res,
+__device__ __noinline__ void trace_deep(const TraceCtx& C, const Seg& s, int64_t i, Result& res,
                                         TravStats& st) {
     res.count = 0;
     res.best = -1;
     res.b64 = false;
-    trace<MODE, 64, STATS>(s, A, B, i, root, nodes, tris, treelet, snodes, S, max_visits, status,
-                           res, st);
+    trace<MODE, 64, STATS>(C, s, i, res, st);
 }
 
 __device__ __forceinline__ void result_init(Result& r) {
@@ -221,8 +315,10 @@ __device__ __forceinline__ void result_init(Result& r) {
     r.b64 = false;
 }
 
-// Nearest outputs; (t, u, v) are recomputed in FP64 when their FP32 error
-// bound could move the point by more than about 2^-21.
+// Nearest outputs; (t, u, v) are recomputed in double-float when their FP32
+// error bound could move the point by more than about 2^-21 (the sign of a
+// sign-normalised det cannot change there: the hit was already decided), and
+// in FP64 for segments whose direction is outside the FP32 filter's range.
 template <bool STATS>
 __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, const float* B,
                                                int64_t i, const float4* __restrict__ tris,
@@ -232,26 +328,35 @@ __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, con
     u = res.bu;
     v = res.bv;
     const float thresh = 0x1p-21f / fmaxf(1.f, s.md * 1.7320508f);
-    if (res.berr > thresh || s.fp64only) {
+    const int p = res.bpos;
+    if (s.fp64only) {
         if (STATS) ++st.refines;
         double tuv[3] = {0.0, 0.0, 0.0};
-        const int p = res.bpos;
         mt64(A[3 * i], A[3 * i + 1], A[3 * i + 2], B[3 * i], B[3 * i + 1], B[3 * i + 2],
              ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
              ld4(tris + 3 * (int64_t)p + 2), tuv);
         t = (float)tuv[0];
         u = (float)tuv[1];
         v = (float)tuv[2];
-        if (s.fp64only) {
-            double dd = 0.0;
-            for (int k = 0; k < 3; ++k) {
-                const double a = A[3 * i + k], d = (double)B[3 * i + k] - a;
-                P[k] = (float)(a + tuv[0] * d);
-                dd += d * d;
-            }
-            dist = (float)(tuv[0] * sqrt(dd));
-            return;
+        double dd = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double a = A[3 * i + k], d = (double)B[3 * i + k] - a;
+            P[k] = (float)(a + tuv[0] * d);
+            dd += d * d;
         }
+        dist = (float)(tuv[0] * sqrt(dd));
+        return;
+    }
+    if (res.berr > thresh) {
+        if (STATS) ++st.refines;
+        const float a3[3] = {s.ax, s.ay, s.az};
+        const float b3[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
+        float tuv[3];
+        mt_df(a3, b3, ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
+              ld4(tris + 3 * (int64_t)p + 2), tuv);
+        t = tuv[0];
+        u = tuv[1];
+        v = tuv[2];
     }
     P[0] = fmaf(t, s.dx, s.ax);
     P[1] = fmaf(t, s.dy, s.ay);
@@ -317,51 +422,109 @@ __device__ __forceinline__ void compact(const TravOut& o, bool has, int64_t i, c
     }
 }
 
-// One segment end to end: setup, traversal (+ deep re-run), dense outputs,
-// compaction.  All lanes of the warp call it (i >= nR for idle lanes).
-template <int MODE, int STACK, bool STATS>
-__device__ __forceinline__ void process_segment(const float* A, const float* B, int64_t nR,
-                                                int64_t i, int root,
-                                                const float4* __restrict__ nodes,
-                                                const float4* __restrict__ tris,
-                                                const float4* __restrict__ treelet,
-                                                const float4* snodes, int S, int max_visits,
-                                                int32_t* status, const TravOut& o,
-                                                TravStats& st) {
+constexpr int kFetchChunk = 128;  // segments a warp takes from the global counter at once
+
+// Persistent per-warp traversal loop over segments [lo, hi).  Every lane
+// holds one segment and advances it by one node per iteration; a lane whose
+// segment finishes takes the next one from the warp's pool right away, so the
+// warp does not idle behind its slowest lane.  The pool is refilled with
+// kFetchChunk segments from *counter (one atomic per chunk), or, with
+// counter == nullptr, holds the whole range [lo, hi) from the start.  When
+// `order` is given, pool position k processes segment order[k] (a coherent
+// ordering of the segments); outputs still go to the segment's own index.
+// Dense outputs are written as segments finish; compaction is
+// warp-aggregated.  Must be called by all 32 lanes of the warp.
+template <int MODE, int STACK, bool STATS, int W>
+__device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long* counter,
+                                           int64_t lo, int64_t hi, TravStats& st,
+                                           unsigned long long& segs) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int64_t pool = lo, pool_end = counter ? lo : hi;
+    bool more = counter != nullptr;
+    int64_t i = -1;
+    Seg s;
+    int node = 0, sp = 0, visits = 0;
+    float tlim = 1.f;
     Result res;
     result_init(res);
-    float dist = 0.f, P[3] = {0.f, 0.f, 0.f};
-    const bool valid = i < nR;
-    if (valid) {
-        Seg s;
-        const bool seg_ok = seg_setup(A, B, i, s);
-        if (seg_ok && root != kNoRoot) {
-            const bool ok = trace<MODE, STACK, STATS>(s, A, B, i, root, nodes, tris, treelet,
-                                                      snodes, S, max_visits, status, res, st);
-            if (STACK < 64 && !ok) {
-                if (STATS) ++st.overflows;
-                trace_deep<MODE, STATS>(s, A, B, i, root, nodes, tris, treelet, snodes, S,
-                                        max_visits, status, res, st);
+    int stack[STACK];
+    while (true) {
+        unsigned idle = __ballot_sync(FULL, i < 0);
+        while (idle) {
+            if (pool >= pool_end) {
+                if (!more) break;
+                unsigned long long b = 0ull;
+                if (lane == 0) b = atomicAdd(counter, (unsigned long long)kFetchChunk);
+                b = __shfl_sync(FULL, b, 0);
+                if (b >= (unsigned long long)hi) {
+                    more = false;
+                    break;
+                }
+                pool = (int64_t)b;
+                pool_end = pool + kFetchChunk < hi ? pool + kFetchChunk : hi;
+            }
+            const int64_t left = pool_end - pool;
+            const int avail = left < (int64_t)__popc(idle) ? (int)left : __popc(idle);
+            if (i < 0 && (int)__popc(idle & lt) < avail) {
+                int64_t k = pool + __popc(idle & lt);
+                if (C.order) k = C.order[k];
+                if (STATS) ++segs;
+                result_init(res);
+                if (seg_setup(C.A, C.B, k, s) && C.root != kNoRoot) {
+                    i = k;
+                    node = W == 4 ? C.root4 : C.root;
+                    sp = 0;
+                    visits = 0;
+                    tlim = 1.f;
+                } else {  // non-finite segment or empty mesh: a miss
+                    float dist, P[3];
+                    write_result<MODE, STATS>(C.out, s, false, C.A, C.B, k, C.tris, res, dist, P,
+                                              st);
+                }
+            }
+            pool += avail;
+            idle = __ballot_sync(FULL, i < 0);
+        }
+        if (__ballot_sync(FULL, i >= 0) == 0u) break;
+        bool fin = false;
+        float dist = 0.f, P[3] = {0.f, 0.f, 0.f};
+        if (i >= 0) {
+            bool overflow = false;
+            if (W == 4)
+                fin = node_step4<MODE, STACK, STATS>(C, s, i, node, sp, stack, tlim, res, visits,
+                                                     overflow, st);
+            else
+                fin = node_step<MODE, STACK, STATS>(C, s, i, node, sp, stack, tlim, res, visits,
+                                                    overflow, st);
+            if (fin) {
+                // a binary traversal needs at most 63 entries; a 4-wide one may
+                // push up to 3 per level and re-runs in binary on overflow
+                if ((STACK < 64 || W == 4) && overflow) {
+                    if (STATS) ++st.overflows;
+                    trace_deep<MODE, STATS>(C, s, i, res, st);
+                }
+                write_result<MODE, STATS>(C.out, s, true, C.A, C.B, i, C.tris, res, dist, P, st);
             }
         }
-        write_result<MODE, STATS>(o, s, seg_ok, A, B, i, tris, res, dist, P, st);
+        if (MODE != RSI_MODE_BOOL && C.out.hit_idx)
+            compact<MODE>(C.out, fin && res.count > 0, i, res, dist, P);
+        if (fin) i = -1;
     }
-    if (MODE != RSI_MODE_BOOL && o.hit_idx) compact<MODE>(o, valid && res.count > 0, i, res, dist, P);
 }
 
 // Sum the per-thread counters of a warp into the global stats.
 __device__ __forceinline__ void flush_stats(const TravStats& st, unsigned long long* g,
                                             unsigned long long segs) {
-    unsigned long long v[5] = {st.visits, st.tests, st.fp64, st.refines, st.overflows};
+    unsigned long long v[6] = {segs, st.visits, st.tests, st.fp64, st.refines, st.overflows};
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 6; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(g + 0, segs);
-        for (int k = 0; k < 5; ++k) atomicAdd(g + 1 + k, v[k]);
-    }
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 6; ++k) atomicAdd(g + k, v[k]);
 }
 
 }  // namespace rsi

@@ -69,7 +69,9 @@ def test_small_build_options(small, leaf, levels):
 @pytest.mark.parametrize("launch", [
     dict(block_size=32), dict(block_size=128, smem_nodes=-1), dict(block_size=512),
     dict(block_size=1024, smem_nodes=2047), dict(stack_depth=16), dict(stack_depth=32),
-    dict(smem_nodes=1)])
+    dict(smem_nodes=1), dict(sort_bits=24), dict(sort_bits=6), dict(sort_bits=30),
+    dict(sort_bits=-1), dict(sort_bits=15, stack_depth=16, block_size=64),
+    dict(node_width=2), dict(node_width=4, stack_depth=16), dict(node_width=2, sort_bits=21)])
 def test_small_launch_options(small, launch):
     mesh, seg, ref = small
     bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
