@@ -63,9 +63,11 @@ typedef enum {
     RSI_ERR_STACK_OVERFLOW = 5, /* traversal stack too small (never with depth >= 64) */
     RSI_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
     RSI_ERR_NOT_BUILT = 7,      /* handle has no built tree */
-    RSI_ERR_INTERNAL = 8        /* a device-side consistency bound was hit (a
+    RSI_ERR_INTERNAL = 8,       /* a device-side consistency bound was hit (a
                                    climb longer than any radix tree, or more
                                    node visits than nodes); the work stopped */
+    RSI_ERR_CAPACITY = 9        /* the problem exceeds the fixed scratch of an
+                                   allocation-free entry point */
 } rsi_status;
 
 typedef enum {
@@ -275,6 +277,33 @@ rsi_status rsi_intersect_backward(const float* dV, int64_t nV, const int32_t* dT
                                   const int32_t* dTri, const float* dGradPoint,
                                   const float* dGradTuv, float* dGradV, float* dGradA,
                                   float* dGradB, rsi_stream s);
+
+/* Largest nV accepted by rsi_intersect_backward_static. */
+#define RSI_STATIC_MAX_VERTICES 262144
+
+/* Allocation-free variant of rsi_intersect_backward (the paper has no
+ * counterpart; it has no backward pass).  For callers that cannot allocate
+ * device memory when they call it -- hosts that reserve all device memory at
+ * start-up and forbid later allocation, code running while a CUDA graph is
+ * captured into a memory pool it does not own, or code called from inside an
+ * allocator -- the FP64 vertex accumulator lives in a fixed device array
+ * compiled into the library (RSI_STATIC_MAX_VERTICES vertices, 6 MiB per
+ * device, held until the process exits) instead of a per-call allocation.
+ * Same arguments, outputs and arithmetic as rsi_intersect_backward; no
+ * cudaMalloc / cudaFree or other allocating call is made.
+ *  - nV > RSI_STATIC_MAX_VERTICES returns RSI_ERR_CAPACITY and enqueues
+ *    nothing.
+ *  - The first call on a device (that device current) looks up the array's
+ *    device address; make it before any stream capture begins.
+ *  - All calls share the array: each call clears what it uses first, and
+ *    the array keeps the last call's sums.  Calls whose work overlaps on the
+ *    GPU (e.g. on two unordered streams) race and give wrong gradients. */
+rsi_status rsi_intersect_backward_static(const float* dV, int64_t nV, const int32_t* dT,
+                                         int64_t nT, const float* dA, const float* dB,
+                                         int64_t nR, const int32_t* dTri,
+                                         const float* dGradPoint, const float* dGradTuv,
+                                         float* dGradV, float* dGradA, float* dGradB,
+                                         rsi_stream s);
 
 /* ------------------------------------------------------------ batched --- */
 

@@ -21,6 +21,8 @@ RSI_ERR_STACK_OVERFLOW = 5
 RSI_ERR_TIMEOUT = 6
 RSI_ERR_NOT_BUILT = 7
 RSI_ERR_INTERNAL = 8
+RSI_ERR_CAPACITY = 9
+RSI_STATIC_MAX_VERTICES = 262144
 
 RSI_MODE_BOOL = 0
 RSI_MODE_COUNT = 1
@@ -86,6 +88,8 @@ _PROTOS = {
                                       P(rsi_launch_opts), vp, P(rsi_stats)]),
     "rsi_intersect_backward": (C.c_int, [vp, i64, vp, i64, vp, vp, i64, vp, vp, vp, vp, vp,
                                          vp, vp]),
+    "rsi_intersect_backward_static": (C.c_int, [vp, i64, vp, i64, vp, vp, i64, vp, vp, vp, vp,
+                                                vp, vp, vp]),
     "rsi_batch_create": (C.c_int, [P(rsi_batch_item), i32, P(rsi_build_opts),
                                    P(rsi_launch_opts), vp, P(vp)]),
     "rsi_batch_build": (C.c_int, [vp, vp]),

@@ -213,6 +213,7 @@ const char* rsi_status_string(rsi_status s) {
         case RSI_ERR_TIMEOUT: return "device-side wait timed out";
         case RSI_ERR_NOT_BUILT: return "tree not built";
         case RSI_ERR_INTERNAL: return "device-side consistency bound hit";
+        case RSI_ERR_CAPACITY: return "problem exceeds the static scratch capacity";
     }
     return "unknown status";
 }
