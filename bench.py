@@ -36,6 +36,21 @@ WORKLOAD = "heightfield 123x123 (29,768 tris) x 10M segments, boolean, build+tra
 BYTES_PER_SEG_BOOL = 25     # 24 B of segment endpoints in + 1 B flag out
 BYTES_PER_SEG_NEAREST = 64  # 24 B in + tri, t, u, v, point, dist (40 B) out
 BYTES_PER_SEG_COUNT = 28
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_trace<BOOL> launch on
+# this workload (ncu, profiles/k_trace_bool_paper_scale.md), valid while the
+# traversal sources hash to `sha`; otherwise reported as null
+TRAFFIC = {"sha": "9765ef344519adb1", "bytes": 257_650_432}
+TRAVERSAL_SOURCES = ("traverse_core.cuh", "rsi_internal.cuh", "traverse.cu")
+
+
+def traversal_sha():
+    """First 16 hex digits of sha256 over the traversal kernel sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAVERSAL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2209_02878_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def env_rank():
@@ -169,15 +184,24 @@ def run_ours(args):
 
     with torch.cuda.stream(stream):
         bvh = rsi.BVH(V, T, stream=stream)
-        kernels_per_step = 2 + 3 * 4 + 1 + 1 + 1 + 1  # build (17) + traversal (1)
+        kernels_per_step = 2 + 3 * 4 + 1 + 1 + 1  # build (16) + traversal (1)
 
-        def step():
+        def eager_step():
             bvh.build(V, T, stream=stream)
             bvh.intersect(A, B, "bool", out=out, stream=stream)
 
         for _ in range(max(args.warmup, 3)):
-            step()
+            eager_step()
         stream.synchronize()
+        step = eager_step
+        if not args.no_graph:
+            # the whole step (build + traversal, 18 kernels) as one CUDA graph
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                eager_step()
+            step = graph.replay
+            step()
+            stream.synchronize()
         if bvh.status(stream) != 0:
             raise RuntimeError("device status set during warm-up")
         if dist:
@@ -238,7 +262,8 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}, segments sharded per rank",
                    "l2": "inputs larger than L2 (240 MB of segments per step)",
                    "launch": "persistent grid from occupancy, block 128, stack 64, binary nodes, "
-                             "input segment order, no shared-memory treelet"},
+                             "input segment order, no shared-memory treelet",
+                   "graph": not args.no_graph},
         "e2e": {"value": round(world * n_seg / (ms_e2e * 1e-3) / 1e6, 3), "unit": UNIT,
                 "h2d_bytes_per_step": 24 * n_seg, "d2h_bytes_per_step": n_seg,
                 "ms_per_step": round(ms_e2e, 4)},
@@ -246,7 +271,8 @@ def run_ours(args):
         "clocks": clk.summary(),
         "roofline": {"bound": "hbm", "kernel": "k_trace<BOOL>", "achieved": round(achieved, 2),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 5),
-                     "peak_kind": peak_kind, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "traffic": TRAFFIC["bytes"] if traversal_sha() == TRAFFIC["sha"] else None,
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "kernel_ms": round(ms_trav, 4)},
         "breakdown": {"traverse_only_Msegs": round(n_seg / (ms_trav * 1e-3) / 1e6, 3),
@@ -391,6 +417,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="headline workload only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -82,8 +82,11 @@ typedef struct {
     int32_t leaf_size;  /* max triangles per leaf, 1..8 (0 -> 1, the paper's
                            one-triangle leaves, Sec. 3.1) */
     int32_t top_levels; /* breadth-first levels of the tree copied into a
-                           compact top "treelet" that traversal can stage in
-                           shared memory, 0..12 (0 -> 10; -1 -> no treelet) */
+                           compact top "treelet" (at most 2048 nodes) that
+                           traversal can stage in shared memory (launch
+                           option smem_nodes), 1..12; 0 or -1 -> no treelet
+                           (the default: L1 serves the top levels as well on
+                           the paper-scale workload) */
 } rsi_build_opts;
 
 /* Options of one traversal launch.  Zero-initialised = defaults. */

@@ -70,15 +70,12 @@ size_t carve(TreeBufs& tb, int64_t N, int M, int nblk, char* base) {
 
 rsi_status check_build_opts(const rsi_build_opts* o, int32_t* leaf, int32_t* levels) {
     *leaf = 1;
-    *levels = 10;
+    *levels = 0;
     if (!o) return RSI_OK;
     if (o->leaf_size < 0 || o->leaf_size > rsi::kMaxLeaf) return RSI_ERR_ARG;
     if (o->top_levels < -1 || o->top_levels > 12) return RSI_ERR_ARG;
     if (o->leaf_size > 0) *leaf = o->leaf_size;
-    if (o->top_levels == -1)
-        *levels = 0;
-    else if (o->top_levels > 0)
-        *levels = o->top_levels;
+    if (o->top_levels > 0) *levels = o->top_levels;
     return RSI_OK;
 }
 
@@ -155,7 +152,7 @@ rsi::TravOut trav_out(rsi_mode mode, const rsi_output* o) {
 struct rsi_bvh_s {
     int device = 0;
     int64_t nV = 0, nT = 0;
-    int32_t leaf = 1, levels = 10;
+    int32_t leaf = 1, levels = 0;
     TreeBufs tb;
     char* mem = nullptr;
     size_t bytes = 0;

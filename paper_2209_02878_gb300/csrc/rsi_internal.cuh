@@ -117,6 +117,14 @@ __device__ __forceinline__ bool finite3(float x, float y, float z) {
     return isfinite(x) && isfinite(y) && isfinite(z);
 }
 
+// 1/x with at most 1 ulp error (PTX rcp.approx.f32, subnormals kept);
+// 1/(+-0) = +-inf, 1/(+-inf) = +-0.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Per-segment registers of the traversal.
 struct Seg {
     float ax, ay, az;  // start a
@@ -137,9 +145,11 @@ __device__ __forceinline__ bool seg_setup(const float* A, const float* B, int64_
     s.dz = __fsub_rn(bz, az);
     // An overflowing difference (|b - a| > FLT_MAX) gives 1/d = 0: that axis
     // then never culls (conservative) and every decision is taken in FP64.
-    s.ix = __frcp_rn(s.dx);
-    s.iy = __frcp_rn(s.dy);
-    s.iz = __frcp_rn(s.dz);
+    // The reciprocal may be off by 1 ulp (PTX rcp.approx): the slab test's
+    // slack covers it.
+    s.ix = rcp_approx(s.dx);
+    s.iy = rcp_approx(s.dy);
+    s.iz = rcp_approx(s.dz);
     s.md = maxabs3(s.dx, s.dy, s.dz);
     const float mn = fminf(fminf(s.dx != 0.f ? fabsf(s.dx) : 1.f, s.dy != 0.f ? fabsf(s.dy) : 1.f),
                            s.dz != 0.f ? fabsf(s.dz) : 1.f);
@@ -150,8 +160,9 @@ __device__ __forceinline__ bool seg_setup(const float* A, const float* B, int64_
 
 // Conservative segment / box test.  Per axis the entry parameter uses the
 // near face and the exit the far face (chosen by the sign of 1/d), computed
-// as (face - a) * (1/d): each has relative error <= 3u, so scaling the exit
-// by 1 + 2^-18 before `entry <= exit` never rejects a box the exact segment
+// as (face - a) * (1/d): with d rounded (u), 1/d within 1 ulp (2u) and two
+// more roundings, each has relative error <= 5u, so scaling the exit by
+// 1 + 2^-18 before `entry <= exit` never rejects a box the exact segment
 // a + s d, s in [0, tlim], touches.  A zero direction component gives
 // (face - a) * inf = +-inf (correct limit) or NaN when the segment lies in
 // the face plane; fmaxf / fminf drop NaN, which is the right answer there.

@@ -58,7 +58,7 @@ def test_small_heightfield_all_modes(small):
     assert ref["flag"].mean() > 0.3  # the workload does cross the surface
 
 
-@pytest.mark.parametrize("leaf,levels", [(1, 0), (1, -1), (2, 4), (4, 10), (8, 12)])
+@pytest.mark.parametrize("leaf,levels", [(1, 0), (1, -1), (1, 10), (2, 4), (4, 10), (8, 12)])
 def test_small_build_options(small, leaf, levels):
     mesh, seg, ref = small
     bvh = rsi.BVH(dev(mesh.V), dev(mesh.T), leaf_size=leaf, top_levels=levels)
@@ -74,7 +74,9 @@ def test_small_build_options(small, leaf, levels):
     dict(node_width=2), dict(node_width=4, stack_depth=16), dict(node_width=2, sort_bits=21)])
 def test_small_launch_options(small, launch):
     mesh, seg, ref = small
-    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    # shared-memory staging needs the breadth-first treelet
+    levels = 11 if launch.get("smem_nodes", 0) > 0 else 0
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T), top_levels=levels)
     compare(run_all_modes(bvh, dev(seg.A), dev(seg.B), launch=launch), ref, what=str(launch))
 
 
