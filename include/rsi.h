@@ -94,7 +94,7 @@ typedef struct {
     int32_t block_size;  /* threads per block, multiple of 32 in [32, 1024]
                             (0 -> 128); capped at what the kernel's register
                             use allows */
-    int32_t stack_depth; /* per-segment traversal stack entries: 16, 32 or 64
+    int32_t stack_depth; /* per-segment traversal stack entries: 8, 32 or 64
                             (0 -> 64).  Radix trees over 64-bit keys are at
                             most 63 levels deep, so 64 never overflows; a
                             smaller stack re-runs overflowed segments with a
@@ -250,6 +250,36 @@ rsi_status rsi_bvh_export(rsi_bvh h, rsi_stream s, float* bounds, uint32_t* code
 rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR,
                          rsi_mode mode, const rsi_output* out,
                          const rsi_launch_opts* lo, rsi_stream s);
+
+/* rsi_intersect from HOST buffers: hA, hB float[nR][3] and the outputs in
+ * *hout (flag / count / tri, tuv, point, dist as for rsi_intersect) are host
+ * pointers; compaction (hout->hit_idx) is not supported.  The segments go
+ * through in chunks of `chunk` (0 -> 2^20) on two internal streams with
+ * double-buffered device staging (56 B per segment per buffer, allocated by
+ * the handle on first use, cudaMallocAsync on s), so that the copy of one
+ * chunk to the device, the traversal of the previous one and the copy of
+ * results back overlap.  The work is ordered after everything already on s,
+ * and s waits for it: the host outputs are complete once s is synchronised.
+ * With pageable host memory the copies are staged by the driver and overlap
+ * less; pinned memory gives full overlap.  Segments are processed in input
+ * order (lo->sort_bits is ignored).  Errors as rsi_intersect, plus
+ * RSI_ERR_OOM. */
+rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64_t nR,
+                              rsi_mode mode, const rsi_output* hout, int64_t chunk,
+                              const rsi_launch_opts* lo, rsi_stream s);
+
+/* Odd-parity inside test for a CLOSED mesh (Sec. 2.6: the crossing count of
+ * the intercept_count mode tells which segment starting points lie inside a
+ * closed surface).  For each point dP[i] (float[nP][3], device) the segment
+ * from the point to a far point along a fixed oblique direction, beyond the
+ * mesh box, is counted in COUNT mode; dInside[i] (uint8[nP], device) = count
+ * mod 2.  A point whose test segment passes within the near-degenerate band
+ * of an edge or vertex can get the wrong parity, as with any parity test.
+ * Uses a workspace of 16 B per point held by the handle (allocated on first
+ * use, cudaMallocAsync on s).  lo as for rsi_intersect (may be NULL).
+ * Errors: RSI_ERR_ARG, RSI_ERR_NOT_BUILT, RSI_ERR_OOM, RSI_ERR_CUDA. */
+rsi_status rsi_points_inside(rsi_bvh h, const float* dP, int64_t nP, uint8_t* dInside,
+                             const rsi_launch_opts* lo, rsi_stream s);
 
 /* Like rsi_intersect with lo->stats set; synchronises s and returns the
  * counters of that launch in *st (host). */

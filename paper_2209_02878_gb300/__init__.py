@@ -185,6 +185,50 @@ class BVH:
                            "rsi_intersect")
         return o
 
+    def intersect_host(self, A, B, mode="bool", *, out=None, chunk=0, launch=None,
+                       stream=None):
+        """Test segments held in HOST memory (float32 [nR,3] CPU tensors; pin
+        them for overlap) with the chunked copy / traverse / copy-back
+        pipeline of rsi_intersect_host.  Returns a dict of host output
+        tensors (pinned when allocated here), complete once `stream` (default
+        current) is synchronised."""
+        for t, nme in ((A, "A"), (B, "B")):
+            if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32 or \
+                    t.dim() != 2 or t.shape[1] != 3 or not t.is_contiguous():
+                raise ValueError(f"{nme} must be a contiguous float32 [n,3] CPU tensor")
+        m = _mode(mode)
+        n = int(A.shape[0])
+        if out is None:
+            pin = torch.cuda.is_available()
+            if m == _abi.RSI_MODE_BOOL:
+                out = {"flag": torch.empty(n, dtype=torch.uint8, pin_memory=pin)}
+            elif m == _abi.RSI_MODE_COUNT:
+                out = {"count": torch.empty(n, dtype=torch.int32, pin_memory=pin)}
+            else:
+                out = {"tri": torch.empty(n, dtype=torch.int32, pin_memory=pin),
+                       "tuv": torch.empty((n, 3), dtype=torch.float32, pin_memory=pin),
+                       "point": torch.empty((n, 3), dtype=torch.float32, pin_memory=pin),
+                       "dist": torch.empty(n, dtype=torch.float32, pin_memory=pin)}
+        ro = _rsi_output(out)
+        lo = _launch(launch)
+        with torch.cuda.device(self.device):
+            _abi.check(self._lib.rsi_intersect_host(self._h, _vp(A), _vp(B), n, m, C.byref(ro),
+                                                    int(chunk), C.byref(lo), _stream(stream)),
+                       "rsi_intersect_host")
+        return out
+
+    def points_inside(self, P, *, launch=None, stream=None):
+        """Odd-parity inside test of points P (float32 [n,3], CUDA) against
+        a closed mesh (rsi_points_inside); returns uint8 [n] (1 = inside)."""
+        _check_tensor(P, "P", torch.float32)
+        out = torch.empty(int(P.shape[0]), dtype=torch.uint8, device=P.device)
+        lo = _launch(launch)
+        with torch.cuda.device(self.device):
+            _abi.check(self._lib.rsi_points_inside(self._h, _vp(P), int(P.shape[0]), _vp(out),
+                                                   C.byref(lo), _stream(stream)),
+                       "rsi_points_inside")
+        return out
+
     def export(self, stream=None) -> dict:
         """Copy the tree to host numpy arrays (synchronises); for validation."""
         n = self.nT

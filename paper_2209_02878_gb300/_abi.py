@@ -84,6 +84,9 @@ _PROTOS = {
     "rsi_bvh_destroy": (C.c_int, [vp]),
     "rsi_bvh_export": (C.c_int, [vp, vp] + [vp] * 9),
     "rsi_intersect": (C.c_int, [vp, vp, vp, i64, C.c_int, P(rsi_output), P(rsi_launch_opts), vp]),
+    "rsi_intersect_host": (C.c_int, [vp, vp, vp, i64, C.c_int, P(rsi_output), i64,
+                                     P(rsi_launch_opts), vp]),
+    "rsi_points_inside": (C.c_int, [vp, vp, i64, vp, P(rsi_launch_opts), vp]),
     "rsi_intersect_stats": (C.c_int, [vp, vp, vp, i64, C.c_int, P(rsi_output),
                                       P(rsi_launch_opts), vp, P(rsi_stats)]),
     "rsi_intersect_backward": (C.c_int, [vp, i64, vp, i64, vp, vp, i64, vp, vp, vp, vp, vp,

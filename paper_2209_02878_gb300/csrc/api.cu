@@ -29,6 +29,7 @@ namespace {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr int kDefaultBlock = 128;
+constexpr int64_t kHostChunk = (int64_t)1 << 20;  // segments per pipeline chunk
 
 // Carves the device buffers of a tree over N triangles and M meshes out of
 // one allocation.  With base == nullptr only the total size is computed.
@@ -98,7 +99,7 @@ rsi_status check_launch_opts(const rsi_launch_opts* lo, bool has_treelet, Launch
             c->block = lo->block_size;
         }
         if (lo->stack_depth != 0) {
-            if (lo->stack_depth != 16 && lo->stack_depth != 32 && lo->stack_depth != 64)
+            if (lo->stack_depth != 8 && lo->stack_depth != 32 && lo->stack_depth != 64)
                 return RSI_ERR_ARG;
             c->stack = lo->stack_depth;
         }
@@ -162,6 +163,16 @@ struct rsi_bvh_s {
     char* seg_mem = nullptr;  // segment-order workspace (grown on demand)
     rsi::SegOrderWs seg_ws{};
     cudaStream_t seg_stream = nullptr;
+    // host-buffer pipeline (rsi_intersect_host): two streams, double buffers
+    cudaStream_t pst[2] = {nullptr, nullptr};
+    cudaEvent_t pev_start = nullptr, pev_done[2] = {nullptr, nullptr};
+    char* pipe_mem = nullptr;
+    int64_t pipe_cap = 0;
+    cudaStream_t pipe_stream = nullptr;
+    // odd-parity workspace (rsi_points_inside): segment ends + counts
+    char* in_mem = nullptr;
+    int64_t in_cap = 0;
+    cudaStream_t in_stream = nullptr;
 };
 
 namespace {
@@ -340,6 +351,13 @@ rsi_status rsi_bvh_destroy(rsi_bvh h) {
     cudaGetDevice(&cur);
     if (cur != h->device) cudaSetDevice(h->device);
     if (h->seg_mem) cudaFreeAsync(h->seg_mem, h->seg_stream);
+    if (h->pipe_mem) cudaFreeAsync(h->pipe_mem, h->pipe_stream);
+    if (h->in_mem) cudaFreeAsync(h->in_mem, h->in_stream);
+    for (int q = 0; q < 2; ++q) {
+        if (h->pst[q]) cudaStreamDestroy(h->pst[q]);
+        if (h->pev_done[q]) cudaEventDestroy(h->pev_done[q]);
+    }
+    if (h->pev_start) cudaEventDestroy(h->pev_start);
     cudaError_t e = cudaFreeAsync(h->mem, h->stream);
     if (cur != h->device) cudaSetDevice(cur);
     delete h;
@@ -407,7 +425,8 @@ rsi_status rsi_bvh_export(rsi_bvh h, rsi_stream s, float* bounds, uint32_t* code
 
 static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, int64_t nR,
                                  rsi_mode mode, const rsi_output* out, const rsi_launch_opts* lo,
-                                 rsi_stream s, bool force_stats) {
+                                 rsi_stream s, bool force_stats,
+                                 unsigned long long* work = nullptr) {
     if (!h || nR < 0) return RSI_ERR_ARG;
     if (mode != RSI_MODE_BOOL && mode != RSI_MODE_COUNT && mode != RSI_MODE_NEAREST)
         return RSI_ERR_ARG;
@@ -443,7 +462,7 @@ static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, in
     P.treelet = h->tb.treelet;
     P.treelet_n = h->tb.treelet_n;
     P.smem_nodes = c.smem_nodes;
-    P.work = h->scratch;
+    P.work = work ? work : h->scratch;
     P.stats = h->scratch + 1;
     P.max_visits = (int)h->nT + 2;
     P.status = h->tb.status;
@@ -482,6 +501,141 @@ rsi_status rsi_intersect_stats(rsi_bvh h, const float* dA, const float* dB, int6
     stt->fp64_tests = (int64_t)v[3];
     stt->fp64_refines = (int64_t)v[4];
     stt->overflows = (int64_t)v[5];
+    return RSI_OK;
+}
+
+// Bytes of device staging per segment and buffer in rsi_intersect_host.
+static int64_t pipe_bytes_per_seg() { return 24 + 32; }
+
+rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64_t nR,
+                              rsi_mode mode, const rsi_output* hout, int64_t chunk,
+                              const rsi_launch_opts* lo, rsi_stream s) {
+    if (!h || nR < 0 || chunk < 0) return RSI_ERR_ARG;
+    if (mode != RSI_MODE_BOOL && mode != RSI_MODE_COUNT && mode != RSI_MODE_NEAREST)
+        return RSI_ERR_ARG;
+    if (!h->built) return RSI_ERR_NOT_BUILT;
+    if (nR == 0) return RSI_OK;
+    if (!hA || !hB) return RSI_ERR_ARG;
+    rsi_status st = check_output(mode, hout);
+    if (st != RSI_OK) return st;
+    if (hout->hit_idx) return RSI_ERR_ARG;  // no compaction from host buffers
+    rsi_launch_opts lo2;
+    memset(&lo2, 0, sizeof(lo2));
+    if (lo) lo2 = *lo;
+    lo2.sort_bits = -1;  // the segment-order workspace is shared: keep input order
+    lo2.stats = 0;
+    const int64_t ch = chunk > 0 ? (chunk < nR ? chunk : nR) : (nR < kHostChunk ? nR : kHostChunk);
+    cudaStream_t cs = (cudaStream_t)s;
+    if (!h->pst[0]) {
+        for (int q = 0; q < 2; ++q) {
+            RSI_CK(cudaStreamCreateWithFlags(&h->pst[q], cudaStreamNonBlocking));
+            RSI_CK(cudaEventCreateWithFlags(&h->pev_done[q], cudaEventDisableTiming));
+        }
+        RSI_CK(cudaEventCreateWithFlags(&h->pev_start, cudaEventDisableTiming));
+    }
+    if (h->pipe_cap < ch) {
+        if (h->pipe_mem) {
+            RSI_CK(cudaFreeAsync(h->pipe_mem, h->pipe_stream));
+            h->pipe_mem = nullptr;
+        }
+        cudaError_t e =
+            cudaMallocAsync((void**)&h->pipe_mem, (size_t)(2 * pipe_bytes_per_seg() * ch + 512), cs);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->pipe_mem = nullptr;
+            h->pipe_cap = 0;
+            return e == cudaErrorMemoryAllocation ? RSI_ERR_OOM : RSI_ERR_CUDA;
+        }
+        h->pipe_cap = ch;
+        h->pipe_stream = cs;
+    }
+    // staging of buffer q: A | B | outputs (flag / count / tri+tuv+point+dist)
+    auto stage = [&](int q) { return h->pipe_mem + (size_t)q * pipe_bytes_per_seg() * h->pipe_cap; };
+    RSI_CK(cudaEventRecord(h->pev_start, cs));
+    for (int q = 0; q < 2; ++q) RSI_CK(cudaStreamWaitEvent(h->pst[q], h->pev_start, 0));
+    int k = 0;
+    for (int64_t off = 0; off < nR; off += ch, ++k) {
+        const int q = k & 1;
+        const int64_t n = nR - off < ch ? nR - off : ch;
+        cudaStream_t S = h->pst[q];
+        char* b = stage(q);
+        float* dA = (float*)b;
+        float* dB = (float*)(b + 12 * h->pipe_cap);
+        char* o = b + 24 * h->pipe_cap;
+        RSI_CK(cudaMemcpyAsync(dA, hA + 3 * off, 12 * (size_t)n, cudaMemcpyHostToDevice, S));
+        RSI_CK(cudaMemcpyAsync(dB, hB + 3 * off, 12 * (size_t)n, cudaMemcpyHostToDevice, S));
+        rsi_output dout;
+        memset(&dout, 0, sizeof(dout));
+        if (mode == RSI_MODE_BOOL) {
+            dout.flag = (uint8_t*)o;
+        } else if (mode == RSI_MODE_COUNT) {
+            dout.count = (int32_t*)o;
+        } else {
+            dout.tri = (int32_t*)o;
+            dout.tuv = (float*)(o + 4 * h->pipe_cap);
+            dout.point = (float*)(o + 16 * h->pipe_cap);
+            dout.dist = (float*)(o + 28 * h->pipe_cap);
+        }
+        st = intersect_impl(h, dA, dB, n, mode, &dout, &lo2, (rsi_stream)S, false,
+                            h->scratch + 8 + q);
+        if (st != RSI_OK) return st;
+        auto back = [&](void* host, const void* dev, size_t bytes) -> cudaError_t {
+            return host ? cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, S)
+                        : cudaSuccess;
+        };
+        if (mode == RSI_MODE_BOOL) {
+            RSI_CK(back(hout->flag + off, dout.flag, (size_t)n));
+        } else if (mode == RSI_MODE_COUNT) {
+            RSI_CK(back(hout->count + off, dout.count, 4 * (size_t)n));
+        } else {
+            RSI_CK(back(hout->tri + off, dout.tri, 4 * (size_t)n));
+            if (hout->tuv) RSI_CK(back(hout->tuv + 3 * off, dout.tuv, 12 * (size_t)n));
+            if (hout->point) RSI_CK(back(hout->point + 3 * off, dout.point, 12 * (size_t)n));
+            if (hout->dist) RSI_CK(back(hout->dist + off, dout.dist, 4 * (size_t)n));
+        }
+    }
+    for (int q = 0; q < 2; ++q) {
+        RSI_CK(cudaEventRecord(h->pev_done[q], h->pst[q]));
+        RSI_CK(cudaStreamWaitEvent(cs, h->pev_done[q], 0));
+    }
+    return RSI_OK;
+}
+
+rsi_status rsi_points_inside(rsi_bvh h, const float* dP, int64_t nP, uint8_t* dInside,
+                             const rsi_launch_opts* lo, rsi_stream s) {
+    if (!h || nP < 0) return RSI_ERR_ARG;
+    if (!h->built) return RSI_ERR_NOT_BUILT;
+    if (nP == 0) return RSI_OK;
+    if (!dP || !dInside) return RSI_ERR_ARG;
+    cudaStream_t cs = (cudaStream_t)s;
+    if (h->nT == 0) {
+        RSI_CK(cudaMemsetAsync(dInside, 0, (size_t)nP, cs));
+        return RSI_OK;
+    }
+    if (h->in_cap < nP) {
+        if (h->in_mem) {
+            RSI_CK(cudaFreeAsync(h->in_mem, h->in_stream));
+            h->in_mem = nullptr;
+        }
+        cudaError_t e = cudaMallocAsync((void**)&h->in_mem, (size_t)(16 * nP + 512), cs);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->in_mem = nullptr;
+            h->in_cap = 0;
+            return e == cudaErrorMemoryAllocation ? RSI_ERR_OOM : RSI_ERR_CUDA;
+        }
+        h->in_cap = nP;
+        h->in_stream = cs;
+    }
+    float* dB = (float*)h->in_mem;
+    int32_t* cnt = (int32_t*)(h->in_mem + align256(12 * (size_t)h->in_cap));
+    RSI_CK(rsi::launch_inside_segments(dP, nP, h->tb.rootbox, dB, cs));
+    rsi_output o;
+    memset(&o, 0, sizeof(o));
+    o.count = cnt;
+    const rsi_status st = intersect_impl(h, dP, dB, nP, RSI_MODE_COUNT, &o, lo, s, false);
+    if (st != RSI_OK) return st;
+    RSI_CK(rsi::launch_parity(cnt, nP, dInside, cs));
     return RSI_OK;
 }
 

@@ -62,7 +62,7 @@ __global__ void k_zero_counts(const BatchItemDev* items, int n) {
 
 const void* batch_kernel(int stack) {
     switch (stack) {
-        case 16: return (const void*)k_batch<16>;
+        case 8: return (const void*)k_batch<8>;
         case 32: return (const void*)k_batch<32>;
         default: return (const void*)k_batch<64>;
     }
@@ -81,7 +81,7 @@ cudaError_t launch_batch(const BatchParams& P, int block, int stack, cudaStream_
     if (e != cudaSuccess) return e;
     k_zero_counts<<<(P.n_items + 255) / 256, 256, 0, s>>>(P.items, P.n_items);
     switch (stack) {
-        case 16: k_batch<16><<<grid, block, 0, s>>>(P); break;
+        case 8: k_batch<8><<<grid, block, 0, s>>>(P); break;
         case 32: k_batch<32><<<grid, block, 0, s>>>(P); break;
         default: k_batch<64><<<grid, block, 0, s>>>(P); break;
     }

@@ -53,6 +53,11 @@ cudaError_t segment_order(const float* A, const float* B, int n, const float4* r
                           SegOrderWs& ws, cudaStream_t s, const int32_t** order);
 int segment_order_launches(int bits);
 
+// Odd-parity classification helpers (inside.cu).
+cudaError_t launch_inside_segments(const float* P, int64_t n, const float4* rootbox, float* B,
+                                   cudaStream_t s);
+cudaError_t launch_parity(const int32_t* count, int64_t n, uint8_t* out, cudaStream_t s);
+
 // Adjoint of the nearest outputs (2 kernels + stream-ordered FP64 scratch).
 cudaError_t launch_backward(const float* V, int64_t nV, const int32_t* T, int64_t nT,
                             const float* A, const float* B, int64_t nR, const int32_t* tri,

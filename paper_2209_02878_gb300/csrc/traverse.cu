@@ -48,7 +48,7 @@ using KernelFn = void (*)(TraceParams);
 template <int MODE, bool STATS, int W>
 static KernelFn pick_stack(int stack) {
     switch (stack) {
-        case 16: return k_trace<MODE, 16, STATS, W>;
+        case 8: return k_trace<MODE, 8, STATS, W>;
         case 32: return k_trace<MODE, 32, STATS, W>;
         default: return k_trace<MODE, 64, STATS, W>;
     }

@@ -35,7 +35,7 @@ def _load(path):
 
 
 def autotune(bvh, V, T, A, B, mode="bool", block_sizes=(64, 128, 256, 512),
-             stack_depths=(32, 64), smem_nodes=(-1, 255, 511, 1023), leaf_sizes=(1, 2, 4),
+             stack_depths=(8, 32, 64), smem_nodes=(-1, 255, 511, 1023), leaf_sizes=(1, 2, 4),
              reps=5, cache: str | None = DEFAULT_CACHE, stream=None):
     """Time every combination (the handle is rebuilt per leaf size) and
     return (best launch options dict, best leaf size, table of entries).

@@ -72,3 +72,29 @@ def test_cpu_tensors_are_refused():
     T = torch.zeros((1, 3), dtype=torch.int32)
     with pytest.raises(ValueError, match="CUDA"):
         rsi.BVH(V, T)
+
+
+def test_argument_validation_without_gpu(lib):
+    """Calls that fail validation return RSI_ERR_ARG before touching CUDA."""
+    from paper_2209_02878_gb300 import _abi
+    L = _abi.load()
+    out = _abi.rsi_output()
+    lo = _abi.rsi_launch_opts()
+    assert L.rsi_intersect(None, None, None, 10, 0, ctypes.byref(out), ctypes.byref(lo),
+                           None) == _abi.RSI_ERR_ARG
+    assert L.rsi_intersect_backward(None, -1, None, 0, None, None, 1, None, None, None, None,
+                                    None, None, None) == _abi.RSI_ERR_ARG
+    assert L.rsi_intersect_backward_static(None, 10**9, None, 0, None, None, 1, None, None,
+                                           None, None, None, None,
+                                           None) == _abi.RSI_ERR_CAPACITY
+    assert L.rsi_batch_create(None, 0, None, None, None, ctypes.byref(ctypes.c_void_p())) \
+        == _abi.RSI_ERR_ARG
+    h = ctypes.c_void_p()
+    assert L.rsi_bvh_create(-1, 10, None, None, ctypes.byref(h)) == _abi.RSI_ERR_ARG
+    assert L.rsi_bvh_create(3, 1 << 31, None, None, ctypes.byref(h)) == _abi.RSI_ERR_ARG
+    bo = _abi.rsi_build_opts(9, 0)
+    assert L.rsi_bvh_create(3, 1, ctypes.byref(bo), None, ctypes.byref(h)) == _abi.RSI_ERR_ARG
+    assert L.rsi_points_inside(None, None, 5, None, None, None) == _abi.RSI_ERR_ARG
+    assert L.rsi_intersect_host(None, None, None, 5, 0, ctypes.byref(out), 0, None,
+                                None) == _abi.RSI_ERR_ARG
+    assert L.rsi_bvh_destroy(None) == _abi.RSI_ERR_ARG

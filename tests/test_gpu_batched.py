@@ -85,7 +85,7 @@ def test_autotune_returns_valid_config():
     V, T, A, B = dev(mesh.V), dev(mesh.T), dev(seg.A), dev(seg.B)
     bvh = rsi.BVH(V, T)
     best, leaf, table = tuning.autotune(bvh, V, T, A, B, "bool", block_sizes=(128, 256),
-                                        stack_depths=(32, 64), smem_nodes=(-1, 511),
+                                        stack_depths=(8, 64), smem_nodes=(-1, 511),
                                         leaf_sizes=(1, 4), reps=3, cache=None)
     assert len(table) == 16
     assert best["block_size"] in (128, 256) and leaf in (1, 4)

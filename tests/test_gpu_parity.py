@@ -68,10 +68,10 @@ def test_small_build_options(small, leaf, levels):
 
 @pytest.mark.parametrize("launch", [
     dict(block_size=32), dict(block_size=128, smem_nodes=-1), dict(block_size=512),
-    dict(block_size=1024, smem_nodes=2047), dict(stack_depth=16), dict(stack_depth=32),
+    dict(block_size=1024, smem_nodes=2047), dict(stack_depth=8), dict(stack_depth=32),
     dict(smem_nodes=1), dict(sort_bits=24), dict(sort_bits=6), dict(sort_bits=30),
-    dict(sort_bits=-1), dict(sort_bits=15, stack_depth=16, block_size=64),
-    dict(node_width=2), dict(node_width=4, stack_depth=16), dict(node_width=2, sort_bits=21)])
+    dict(sort_bits=-1), dict(sort_bits=15, stack_depth=8, block_size=64),
+    dict(node_width=2), dict(node_width=4, stack_depth=8), dict(node_width=2, sort_bits=21)])
 def test_small_launch_options(small, launch):
     mesh, seg, ref = small
     # shared-memory staging needs the breadth-first treelet
@@ -249,6 +249,63 @@ def test_refit_moves_with_vertices(small):
     ref = oracle.brute(V2, mesh.T, seg.A, seg.B)
     compare(run_all_modes(bvh, dev(seg.A), dev(seg.B)), ref, what="refit")
     tree_check(bvh.export(), mesh.n_tri)
+
+
+@pytest.mark.parametrize("chunk,pin", [(0, True), (1000, True), (4103, False), (10**9, True)])
+def test_intersect_from_host_buffers(small, chunk, pin):
+    mesh, seg, ref = small
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    A = torch.from_numpy(seg.A)
+    B = torch.from_numpy(seg.B)
+    if pin:
+        A, B = A.pin_memory(), B.pin_memory()
+    s = torch.cuda.Stream()
+    got = {}
+    for m in ("bool", "count", "nearest"):
+        got[m] = bvh.intersect_host(A, B, m, chunk=chunk, stream=s)
+    s.synchronize()
+    got = {m: {k: v.numpy() for k, v in d.items()} for m, d in got.items()}
+    compare(got, ref, what=f"host chunk={chunk}")
+
+
+def test_points_inside_star_shaped_sphere():
+    """Odd parity against the independent radial truth of a star-shaped
+    closed surface: p is inside iff |p| < radius of the surface along p."""
+    rng = np.random.default_rng(9)
+    mesh = synth.icosphere(5, rng)
+    P = rng.uniform(-1.3, 1.3, size=(20000, 3)).astype(np.float32)
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    got = bvh.points_inside(dev(P)).cpu().numpy()
+    rmax = float(np.linalg.norm(mesh.V.astype(np.float64), axis=1).max())
+    u = P.astype(np.float64) / np.linalg.norm(P.astype(np.float64), axis=1, keepdims=True)
+    r = oracle.brute(mesh.V, mesh.T, np.zeros_like(P), (u * rmax * 1.5).astype(np.float32))
+    rs = np.linalg.norm(r["point"], axis=1)
+    rp = np.linalg.norm(P.astype(np.float64), axis=1)
+    ok = (r["count"] == 1) & (r["neardeg"] == 0) & (np.abs(rp - rs) > 1e-4)
+    assert ok.mean() > 0.98
+    np.testing.assert_array_equal(got[ok], (rp < rs)[ok].astype(np.uint8))
+    assert 0.2 < got.mean() < 0.8
+
+
+def test_stack_overflow_reruns_with_deep_stack():
+    """An 8-entry stack overflows on a deep tree; the overflowed segments are
+    re-run with the 64-entry stack and the results do not change."""
+    rng = np.random.default_rng(12)
+    mesh = synth.icosphere(7, rng)                 # 327,680 triangles
+    seg = synth.segments_box(rng, 20000, [-1.5] * 3, [1.5] * 3, [-1.5] * 3, [1.5] * 3)
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    A, B = dev(seg.A), dev(seg.B)
+    deep = {m: bvh.intersect(A, B, m) for m in ("count", "nearest")}
+    for w in (2, 4):
+        small = {m: bvh.intersect(A, B, m, launch=dict(stack_depth=8, node_width=w), stats=True)
+                 for m in ("count", "nearest")}
+        assert small["count"]["stats"]["overflows"] > 0
+        assert torch.equal(small["count"]["count"], deep["count"]["count"])
+        assert torch.equal(small["nearest"]["tri"], deep["nearest"]["tri"])
+        assert torch.equal(small["nearest"]["tuv"], deep["nearest"]["tuv"])
+    idx = np.random.default_rng(0).choice(seg.n, 300, replace=False)
+    ref = oracle.brute(mesh.V, mesh.T, seg.A[idx], seg.B[idx])
+    np.testing.assert_array_equal(deep["count"]["count"].cpu().numpy()[idx], ref["count"])
 
 
 # ------------------------------------------------------------ full sizes
