@@ -228,10 +228,11 @@ rsi_status rsi_bvh_destroy(rsi_bvh h);
  *   range   int32[nT-1][2]  first, last leaf of internal node i
  *   nbox    float[nT-1][6]  internal node boxes (lo xyz, hi xyz)
  *   lbox    float[nT][6]    leaf (triangle) boxes by sorted position
- *   nodes   float[nT][16]   the traversal nodes (slot nT-1 is the root slot):
- *                           child0 lo.xyz, child0 hi.x | child0 hi.yz,
- *                           child1 lo.xy | child1 lo.z, child1 hi.xyz |
- *                           ref0, ref1, cnt0, cnt1 (int32 bit patterns) */
+ *   nodes   float[nT][16]   the traversal nodes (slot nT-1 is the root slot),
+ *                           the children's coordinates in pairs:
+ *                           lo.x0 lo.x1 lo.y0 lo.y1 | lo.z0 lo.z1 hi.x0 hi.x1 |
+ *                           hi.y0 hi.y1 hi.z0 hi.z1 | ref0 ref1 cnt0 cnt1
+ *                           (refs and counts as int32 bit patterns) */
 rsi_status rsi_bvh_export(rsi_bvh h, rsi_stream s, float* bounds, uint32_t* codes,
                           int32_t* order, int32_t* left, int32_t* right, int32_t* range,
                           float* nbox, float* lbox, float* nodes);

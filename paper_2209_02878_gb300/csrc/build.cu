@@ -236,10 +236,11 @@ __device__ __forceinline__ void write_node(float4* nodes, int slot, float4 l0, f
     f[13] = i2f(ref1);
     f[14] = i2f(cnt0);
     f[15] = i2f(cnt1);
+    // the two children's coordinates interleaved in pairs (see rsi_internal.cuh)
     float4* o = nodes + 4 * (int64_t)slot;
-    __stcg(o + 0, make_float4(f[0], f[1], f[2], f[3]));
-    __stcg(o + 1, make_float4(f[4], f[5], f[6], f[7]));
-    __stcg(o + 2, make_float4(f[8], f[9], f[10], f[11]));
+    __stcg(o + 0, make_float4(f[0], f[6], f[1], f[7]));
+    __stcg(o + 1, make_float4(f[2], f[8], f[3], f[9]));
+    __stcg(o + 2, make_float4(f[4], f[10], f[5], f[11]));
     __stcg(o + 3, make_float4(f[12], f[13], f[14], f[15]));
 }
 
@@ -263,10 +264,10 @@ __device__ __forceinline__ void binary_children(const float4* __restrict__ nodes
                                                 Slot4& a, Slot4& b) {
     const float4* p = nodes + 4 * (int64_t)slot;
     const float4 f0 = __ldcg(p), f1 = __ldcg(p + 1), f2 = __ldcg(p + 2), f3 = __ldcg(p + 3);
-    a.lo[0] = f0.x; a.lo[1] = f0.y; a.lo[2] = f0.z;
-    a.hi[0] = f0.w; a.hi[1] = f1.x; a.hi[2] = f1.y;
-    b.lo[0] = f1.z; b.lo[1] = f1.w; b.lo[2] = f2.x;
-    b.hi[0] = f2.y; b.hi[1] = f2.z; b.hi[2] = f2.w;
+    a.lo[0] = f0.x; a.lo[1] = f0.z; a.lo[2] = f1.x;
+    a.hi[0] = f1.z; a.hi[1] = f2.x; a.hi[2] = f2.z;
+    b.lo[0] = f0.y; b.lo[1] = f0.w; b.lo[2] = f1.y;
+    b.hi[0] = f1.w; b.hi[1] = f2.y; b.hi[2] = f2.w;
     a.ref = f2i(f3.x);
     b.ref = f2i(f3.y);
     a.cnt = f2i(f3.z);

@@ -9,10 +9,12 @@
 //   range[2N]        first, last leaf (global sorted positions) of slot g
 //   parent[2N]       [0,N): parent of internal slot, [N,2N): parent of leaf
 //   nbox/lbox[2N]    float4 lo, hi boxes of internal slots / leaves
-//   nodes[4N]        traversal node per slot = 4 x float4 = 64 B:
-//                      {c0.lo.x, c0.lo.y, c0.lo.z, c0.hi.x}
-//                      {c0.hi.y, c0.hi.z, c1.lo.x, c1.lo.y}
-//                      {c1.lo.z, c1.hi.x, c1.hi.y, c1.hi.z}
+//   nodes[4N]        traversal node per slot = 4 x float4 = 64 B, the two
+//                    children's coordinates interleaved in pairs so that one
+//                    packed f32x2 operation serves both child boxes:
+//                      {c0.lo.x, c1.lo.x, c0.lo.y, c1.lo.y}
+//                      {c0.lo.z, c1.lo.z, c0.hi.x, c1.hi.x}
+//                      {c0.hi.y, c1.hi.y, c0.hi.z, c1.hi.z}
 //                      {ref0, ref1, cnt0, cnt1} as int bit patterns
 //                    cnt > 0: leaf of cnt triangles starting at sorted
 //                    position ref; cnt == 0: internal slot ref; cnt == -1:
@@ -133,7 +135,32 @@ struct Seg {
     float md;          // max |d_i|
     bool tiny;         // some 0 < |d_i| < 2^-60: boxes tested by overlap instead
     bool fp64only;     // |d| outside the FP32 filter's range: decide in FP64
+    unsigned long long pax, pay, paz;  // (a_k, a_k) packed for f32x2 arithmetic
+    unsigned long long pix, piy, piz;  // (1/d_k, 1/d_k) packed
 };
+
+// Packed pairs of floats for the f32x2 instructions (one instruction computes
+// the same operation for both children of a node).
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 up2(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 
 __device__ __forceinline__ bool seg_setup(const float* A, const float* B, int64_t i, Seg& s) {
     const float ax = A[3 * i], ay = A[3 * i + 1], az = A[3 * i + 2];
@@ -155,6 +182,12 @@ __device__ __forceinline__ bool seg_setup(const float* A, const float* B, int64_
                            s.dz != 0.f ? fabsf(s.dz) : 1.f);
     s.tiny = mn < kTinyDir;
     s.fp64only = !(s.md >= kRangeLo && s.md <= kRangeHi);
+    s.pax = pk2(ax, ax);
+    s.pay = pk2(ay, ay);
+    s.paz = pk2(az, az);
+    s.pix = pk2(s.ix, s.ix);
+    s.piy = pk2(s.iy, s.iy);
+    s.piz = pk2(s.iz, s.iz);
     return true;
 }
 
@@ -191,6 +224,41 @@ __device__ __forceinline__ bool slab(const Seg& s, float lx, float ly, float lz,
     const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tlim));
     tent = tn;
     return tn <= tf * (1.f + kSlabSlack);
+}
+
+// The slab test of both children of a node at once, on the paired node
+// layout: per axis the near-face and far-face parameters of the two children
+// come from one f32x2 subtraction and one f32x2 multiplication (IEEE RN per
+// lane, the same rounding as the scalar test above).  q0..q2 are the node's
+// first three 16-byte words.
+__device__ __forceinline__ void slab2(const Seg& s, const ulonglong2& q0, const ulonglong2& q1,
+                                      const ulonglong2& q2, float tlim, bool& h0, float& t0,
+                                      bool& h1, float& t1) {
+    const unsigned long long lox = q0.x, loy = q0.y, loz = q1.x;
+    const unsigned long long hix = q1.y, hiy = q2.x, hiz = q2.y;
+    if (s.tiny) {
+        const float2 lx = up2(lox), ly = up2(loy), lz = up2(loz);
+        const float2 hx = up2(hix), hy = up2(hiy), hz = up2(hiz);
+        h0 = slab(s, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, tlim, t0);
+        h1 = slab(s, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, tlim, t1);
+        return;
+    }
+    const bool nx = s.ix < 0.f, ny = s.iy < 0.f, nz = s.iz < 0.f;
+    const float2 tnx = up2(mul2(sub2(nx ? hix : lox, s.pax), s.pix));
+    const float2 tfx = up2(mul2(sub2(nx ? lox : hix, s.pax), s.pix));
+    const float2 tny = up2(mul2(sub2(ny ? hiy : loy, s.pay), s.piy));
+    const float2 tfy = up2(mul2(sub2(ny ? loy : hiy, s.pay), s.piy));
+    const float2 tnz = up2(mul2(sub2(nz ? hiz : loz, s.paz), s.piz));
+    const float2 tfz = up2(mul2(sub2(nz ? loz : hiz, s.paz), s.piz));
+    const float tn0 = fmaxf(fmaxf(tnx.x, tny.x), fmaxf(tnz.x, 0.f));
+    const float tn1 = fmaxf(fmaxf(tnx.y, tny.y), fmaxf(tnz.y, 0.f));
+    const float tf0 = fminf(fminf(tfx.x, tfy.x), fminf(tfz.x, tlim));
+    const float tf1 = fminf(fminf(tfx.y, tfy.y), fminf(tfz.y, tlim));
+    const float2 tf = up2(mul2(pk2(tf0, tf1), pk2(1.f + kSlabSlack, 1.f + kSlabSlack)));
+    t0 = tn0;
+    t1 = tn1;
+    h0 = tn0 <= tf.x;
+    h1 = tn1 <= tf.y;
 }
 
 // FP32 Moller-Trumbore with a static error filter.

@@ -12,8 +12,15 @@
 
 namespace rsi {
 
+// Register caps per mode (measured on the paper-scale workload: fewer
+// registers, more resident warps to hide the dependent node fetches).
+template <int MODE>
+struct TraceRegs {
+    static constexpr int value = MODE == RSI_MODE_BOOL ? 64 : 72;
+};
+
 template <int MODE, int STACK, bool STATS, int W>
-__global__ void k_trace(TraceParams P) {
+__global__ void __maxnreg__(TraceRegs<MODE>::value) k_trace(TraceParams P) {
     extern __shared__ float4 snodes[];
     int S = 0;
     if (P.smem_nodes > 0) {

@@ -157,33 +157,35 @@ __device__ __forceinline__ bool node_step(const TraceCtx& C, const Seg& s, int64
         atomicCAS(C.status, 0, RSI_ERR_INTERNAL);
         return true;
     }
-    float4 n0, n1, n2, n3;
+    ulonglong2 q0, q1, q2;
+    int4 rc;
     if (node < 0) {
         const int k = ~node;
         if (k < C.S) {
-            n0 = C.snodes[4 * k];
-            n1 = C.snodes[4 * k + 1];
-            n2 = C.snodes[4 * k + 2];
-            n3 = C.snodes[4 * k + 3];
+            const ulonglong2* p = (const ulonglong2*)(C.snodes + 4 * k);
+            q0 = p[0];
+            q1 = p[1];
+            q2 = p[2];
+            rc = ((const int4*)p)[3];
         } else {
-            const float4* p = C.treelet + 4 * (int64_t)k;
-            n0 = ld4(p);
-            n1 = ld4(p + 1);
-            n2 = ld4(p + 2);
-            n3 = ld4(p + 3);
+            const ulonglong2* p = (const ulonglong2*)(C.treelet + 4 * (int64_t)k);
+            q0 = __ldg(p);
+            q1 = __ldg(p + 1);
+            q2 = __ldg(p + 2);
+            rc = __ldg((const int4*)p + 3);
         }
     } else {
-        const float4* p = C.nodes + 4 * (int64_t)node;
-        n0 = ld4(p);
-        n1 = ld4(p + 1);
-        n2 = ld4(p + 2);
-        n3 = ld4(p + 3);
+        const ulonglong2* p = (const ulonglong2*)(C.nodes + 4 * (int64_t)node);
+        q0 = __ldg(p);
+        q1 = __ldg(p + 1);
+        q2 = __ldg(p + 2);
+        rc = __ldg((const int4*)p + 3);
     }
     if (STATS) ++st.visits;
     float t0, t1;
-    const bool h0 = slab(s, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, tlim, t0);
-    const bool h1 = slab(s, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, tlim, t1);
-    const int r0 = f2i(n3.x), r1 = f2i(n3.y), c0 = f2i(n3.z), c1 = f2i(n3.w);
+    bool h0, h1;
+    slab2(s, q0, q1, q2, tlim, h0, t0, h1, t1);
+    const int r0 = rc.x, r1 = rc.y, c0 = rc.z, c1 = rc.w;
     if (h0 && c0 > 0 && leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r0, c0, res, tlim, st))
         return true;
     if (h1 && c1 > 0 && leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r1, c1, res, tlim, st))
@@ -232,19 +234,20 @@ __device__ __forceinline__ bool node_step4(const TraceCtx& C, const Seg& s, int6
         atomicCAS(C.status, 0, RSI_ERR_INTERNAL);
         return true;
     }
-    const float4* p = C.nodes4 + 8 * (int64_t)node;
-    const float4 lx = ld4(p), ly = ld4(p + 1), lz = ld4(p + 2);
-    const float4 hx = ld4(p + 3), hy = ld4(p + 4), hz = ld4(p + 5);
-    const float4 rf = ld4(p + 6), ct = ld4(p + 7);
+    const ulonglong2* p = (const ulonglong2*)(C.nodes4 + 8 * (int64_t)node);
+    const ulonglong2 lx = __ldg(p), ly = __ldg(p + 1), lz = __ldg(p + 2);
+    const ulonglong2 hx = __ldg(p + 3), hy = __ldg(p + 4), hz = __ldg(p + 5);
+    const int4 rf = __ldg((const int4*)p + 6), ct = __ldg((const int4*)p + 7);
     if (STATS) ++st.visits;
-    const int r[4] = {f2i(rf.x), f2i(rf.y), f2i(rf.z), f2i(rf.w)};
-    const int c[4] = {f2i(ct.x), f2i(ct.y), f2i(ct.z), f2i(ct.w)};
+    const int r[4] = {rf.x, rf.y, rf.z, rf.w};
+    const int c[4] = {ct.x, ct.y, ct.z, ct.w};
     float t[4];
     bool h[4];
-    h[0] = slab(s, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, tlim, t[0]);
-    h[1] = slab(s, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, tlim, t[1]);
-    h[2] = slab(s, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, tlim, t[2]);
-    h[3] = slab(s, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, tlim, t[3]);
+    // children 0,1 and 2,3 as two packed pairs (SoA words split in halves)
+    slab2(s, make_ulonglong2(lx.x, ly.x), make_ulonglong2(lz.x, hx.x),
+          make_ulonglong2(hy.x, hz.x), tlim, h[0], t[0], h[1], t[1]);
+    slab2(s, make_ulonglong2(lx.y, ly.y), make_ulonglong2(lz.y, hx.y),
+          make_ulonglong2(hy.y, hz.y), tlim, h[2], t[2], h[3], t[3]);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         if (h[q] && c[q] > 0 &&

@@ -37,7 +37,8 @@ def tree_check(exp, nT, leaf_size=1, max_depth=64):
         depth = max(depth, d)
         assert d <= max_depth, "tree deeper than the stack bound"
         for k in range(2):
-            box = f[node, 6 * k:6 * k + 6]
+            # children interleaved: lo.x0 lo.x1 lo.y0 lo.y1 lo.z0 lo.z1 hi.x0 ...
+            box = f[node, [k, 2 + k, 4 + k, 6 + k, 8 + k, 10 + k]]
             ref, cnt = int(ii[node, 12 + k]), int(ii[node, 14 + k])
             if cnt > 0:
                 assert cnt <= leaf_size or node == root, "leaf larger than leaf_size"
@@ -47,11 +48,13 @@ def tree_check(exp, nT, leaf_size=1, max_depth=64):
                 assert np.array_equal(box, union), "leaf box is not the union of its triangles"
             elif ref >= 0:
                 sub = f[ref]
-                lo = np.minimum(sub[0:3], sub[6:9])
-                hi = np.maximum(sub[3:6], sub[9:12])
+                b0 = sub[[0, 2, 4, 6, 8, 10]]
+                b1 = sub[[1, 3, 5, 7, 9, 11]]
+                lo = np.minimum(b0[:3], b1[:3])
+                hi = np.maximum(b0[3:], b1[3:])
                 # an empty second child (root slot) is stored at +inf
-                if np.isinf(sub[6:12]).all():
-                    lo, hi = sub[0:3], sub[3:6]
+                if np.isinf(b1).all():
+                    lo, hi = b0[:3], b0[3:]
                 assert np.array_equal(box, np.r_[lo, hi]), "internal box is not its children's union"
                 stack.append((ref, d + 1))
             else:
