@@ -39,7 +39,7 @@ BYTES_PER_SEG_COUNT = 28
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace<BOOL> launch on
 # this workload (ncu, profiles/k_trace_bool_paper_scale.md), valid while the
 # traversal sources hash to `sha`; otherwise reported as null
-TRAFFIC = {"sha": "9765ef344519adb1", "bytes": 257_650_432}
+TRAFFIC = {"sha": "cf9700a15165dc94", "bytes": 259_822_848}
 TRAVERSAL_SOURCES = ("traverse_core.cuh", "rsi_internal.cuh", "traverse.cu")
 
 

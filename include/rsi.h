@@ -117,8 +117,10 @@ typedef struct {
     int32_t node_width;  /* traversal node arity: 2 (the binary tree, as in
                             the paper) or 4 (each visit tests the four
                             grandchildren of a binary node: half the chain of
-                            dependent node fetches, twice the box tests);
-                            0 -> 2.  smem_nodes > 0 implies 2. */
+                            dependent node fetches, twice the box tests;
+                            its records are built by one extra kernel on the
+                            first 4-wide traversal after each build or
+                            refit); 0 -> 2.  smem_nodes > 0 implies 2. */
 } rsi_launch_opts;
 
 /* Per-segment outputs, all DEVICE pointers owned by the caller.  Which must be

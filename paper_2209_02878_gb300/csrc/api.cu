@@ -43,7 +43,7 @@ size_t carve(TreeBufs& tb, int64_t N, int M, int nblk, char* base) {
     const int64_t n1 = N > 0 ? N : 1;
     tb.N = (int32_t)N;
     tb.M = M;
-    tb.ntiles = (int32_t)((N + rsi::kSortTile - 1) / rsi::kSortTile);
+    tb.ntiles = (int32_t)((N + rsi::kSortTileMin - 1) / rsi::kSortTileMin);
     tb.nblk = nblk;
     tb.keys[0] = (uint64_t*)take(8 * n1);
     tb.keys[1] = (uint64_t*)take(8 * n1);
@@ -159,6 +159,7 @@ struct rsi_bvh_s {
     size_t bytes = 0;
     unsigned long long* scratch = nullptr;  // [0] work counter, [1..6] stats
     bool built = false;
+    bool nodes4_valid = false;  // 4-wide records built for the current tree
     cudaStream_t stream = nullptr;
     char* seg_mem = nullptr;  // segment-order workspace (grown on demand)
     rsi::SegOrderWs seg_ws{};
@@ -183,7 +184,7 @@ rsi_status ensure_seg_ws(rsi_bvh h, int64_t n, cudaStream_t s) {
         cudaFreeAsync(h->seg_mem, s);
         h->seg_mem = nullptr;
     }
-    const int64_t ntiles = (n + rsi::kSortTile - 1) / rsi::kSortTile;
+    const int64_t ntiles = (n + rsi::kSortTileMin - 1) / rsi::kSortTileMin;
     const size_t b1 = align256(4 * (size_t)n);
     const size_t bh = align256(4 * (size_t)rsi::kSortBins * (size_t)(ntiles > 0 ? ntiles : 1));
     const size_t bytes = 4 * b1 + bh + align256(4 * rsi::kSortBins);
@@ -288,6 +289,7 @@ rsi_status rsi_bvh_build(rsi_bvh h, const float* dV, const int32_t* dT, rsi_stre
     h->tb.top_levels = h->levels;
     RSI_CK(rsi::build_tree(h->tb, ma, (cudaStream_t)s, false));
     h->built = true;
+    h->nodes4_valid = false;
     h->stream = (cudaStream_t)s;
     return RSI_OK;
 }
@@ -316,6 +318,7 @@ rsi_status rsi_refit(rsi_bvh h, const float* dV, const int32_t* dT, rsi_stream s
     ma.one.n = (int32_t)h->nT;
     ma.one.nblk = h->tb.nblk;
     RSI_CK(rsi::build_tree(h->tb, ma, (cudaStream_t)s, true));
+    h->nodes4_valid = false;
     h->stream = (cudaStream_t)s;
     return RSI_OK;
 }
@@ -474,6 +477,10 @@ static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, in
         if (st != RSI_OK) return st;
         RSI_CK(rsi::segment_order(dA, dB, (int)nR, h->tb.rootbox, bits, h->seg_ws,
                                   (cudaStream_t)s, &P.order));
+    }
+    if (c.width == 4 && !h->nodes4_valid && h->nT > 0) {  // built on first use
+        RSI_CK(rsi::build_nodes4(h->tb, (cudaStream_t)s));
+        h->nodes4_valid = true;
     }
     if (c.stats) RSI_CK(cudaMemsetAsync(P.stats, 0, 6 * 8, (cudaStream_t)s));
     RSI_CK(rsi::launch_trace(P, mode, c.stack, c.stats, c.block, c.width, (cudaStream_t)s));

@@ -31,6 +31,19 @@ __device__ __forceinline__ void latch(int32_t* status, int code) {
     atomicCAS(status, 0, code);
 }
 
+// atomicAdd with acquire-release semantics at device scope (no separate
+// fences): writes before it are visible to the thread that later reads the
+// value it produced, and writes made visible by earlier releases are seen
+// after it.
+__device__ __forceinline__ int atomic_add_acq_rel(int32_t* p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "l"(p), "r"(v)
+                 : "memory");
+    return old;
+}
+
 // Loads triangle j of mesh md; an index outside [0, nV) latches
 // RSI_ERR_BAD_INDEX and yields vertex 0 (the triangle is then discarded).
 __device__ __forceinline__ bool tri_vertices(const MeshDesc& md, int j, int32_t* status,
@@ -332,7 +345,6 @@ __global__ void k_climb(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ k
     const int m = (int)(keys[g] >> 32);
     if (n == 1) {
         write_root(tb.nodes, root_slot, lo, hi, g, 1);
-        write_node4(tb.nodes, tb.nodes4, root_slot);
         tb.rootbox[2 * m] = lo;
         tb.rootbox[2 * m + 1] = hi;
         return;
@@ -344,9 +356,9 @@ __global__ void k_climb(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ k
             latch(tb.status, RSI_ERR_INTERNAL);
             return;
         }
-        __threadfence();
-        if (atomicAdd(&tb.flag[node], 1) == 0) return;  // the sibling finishes this node
-        __threadfence();
+        // acquire-release: the first arrival publishes its child's box and
+        // node record, the second arrival sees them
+        if (atomic_add_acq_rel(&tb.flag[node], 1) == 0) return;  // the sibling finishes it
         const int ch[2] = {tb.child[2 * node], tb.child[2 * node + 1]};
         float4 cl[2], chh[2];
         int ref[2], cnt[2];
@@ -380,7 +392,6 @@ __global__ void k_climb(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ k
         __stcg(tb.nbox + 2 * (int64_t)node, ulo);
         __stcg(tb.nbox + 2 * (int64_t)node + 1, uhi);
         write_node(tb.nodes, node, cl[0], chh[0], ref[0], cnt[0], cl[1], chh[1], ref[1], cnt[1]);
-        write_node4(tb.nodes, tb.nodes4, node);
         if (node == off) {  // Karras root: fill the root slot
             tb.rootbox[2 * m] = ulo;
             tb.rootbox[2 * m + 1] = uhi;
@@ -388,11 +399,18 @@ __global__ void k_climb(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ k
                 write_root(tb.nodes, root_slot, ulo, uhi, off, n);
             else
                 write_root(tb.nodes, root_slot, ulo, uhi, off, 0);
-            write_node4(tb.nodes, tb.nodes4, root_slot);
             return;
         }
         node = tb.parent[node];
     }
+}
+
+// 4-wide records for every slot of the built tree (one thread per slot, after
+// the climb has written all binary records).  Only needed by 4-wide
+// traversal, so it runs on first use.
+__global__ void k_nodes4(const float4* __restrict__ nodes, float4* __restrict__ nodes4, int N) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < N) write_node4(nodes, nodes4, g);
 }
 
 // ---------------------------------------------------------------- treelet
@@ -514,6 +532,12 @@ cudaError_t build_tree(TreeBufs& tb, const MeshArgs& ma, cudaStream_t s, bool re
     }
     k_climb<<<cdiv(N, 256), 256, 0, s>>>(ma, tb, tb.keys[tb.sorted], tb.vals[tb.sorted]);
     if (tb.M == 1 && tb.top_levels > 0) k_treelet<<<1, 1024, 0, s>>>(tb, N - 1, tb.top_levels);
+    return cudaGetLastError();
+}
+
+cudaError_t build_nodes4(const TreeBufs& tb, cudaStream_t s) {
+    if (tb.N == 0) return cudaSuccess;
+    k_nodes4<<<cdiv(tb.N, 256), 256, 0, s>>>(tb.nodes, tb.nodes4, tb.N);
     return cudaGetLastError();
 }
 

@@ -43,9 +43,10 @@ constexpr int kTreeletMax = 2048;   // nodes in the breadth-first top treelet
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile
+constexpr int kSortTileMin = kSortThreads * 4;         // 1024 keys per tile (small sorts)
 constexpr int kSortBins = 256;
 constexpr int kBuildThreads = 256;
-constexpr int kBuildChunk = 2048;   // triangles per block in bounds / Morton
+constexpr int kBuildChunk = 512;    // triangles per block in bounds / Morton
 
 // FP32 filter constants (see mt32 below).
 constexpr float kFilterK = 0x1p-17f;

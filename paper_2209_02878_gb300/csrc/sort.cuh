@@ -18,16 +18,16 @@
 
 namespace rsi {
 
-template <typename K>
+template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const K* __restrict__ keys, int n,
                                                             int shift, uint32_t* __restrict__ hist,
                                                             int ntiles) {
     __shared__ uint32_t h[kSortBins];
     h[threadIdx.x] = 0;
     __syncthreads();
-    const int base = blockIdx.x * kSortTile;
+    const int base = blockIdx.x * kSortThreads * ITEMS;
 #pragma unroll 4
-    for (int it = 0; it < kSortItems; ++it) {
+    for (int it = 0; it < ITEMS; ++it) {
         const int pos = base + it * kSortThreads + threadIdx.x;
         if (pos < n) atomicAdd(&h[(uint32_t)(keys[pos] >> shift) & 0xffu], 1u);
     }
@@ -82,7 +82,7 @@ static __global__ void __launch_bounds__(256) k_sort_scan(uint32_t* __restrict__
     if (threadIdx.x == 0) totals[blockIdx.x] = tot;
 }
 
-template <typename K>
+template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, int n, int shift, const uint32_t* __restrict__ hist,
@@ -93,11 +93,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     for (int q = threadIdx.x; q < W * kSortBins; q += kSortThreads) (&cnt[0][0])[q] = 0;
     // digit base = exclusive scan of the digit totals
     const uint32_t dbase = block_scan_u32(totals[threadIdx.x], nullptr);  // kSortThreads == bins
-    const int wbase = blockIdx.x * kSortTile + w * (32 * kSortItems);
+    const int wbase = blockIdx.x * (kSortThreads * ITEMS) + w * (32 * ITEMS);
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t local[kSortItems];
+    uint32_t local[ITEMS];
 #pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
+    for (int it = 0; it < ITEMS; ++it) {
         const int pos = wbase + it * 32 + lane;
         const bool valid = pos < n;
         const uint32_t d = valid ? ((uint32_t)(kin[pos] >> shift) & 0xffu) : 0x100u;
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     }
     __syncthreads();
 #pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
+    for (int it = 0; it < ITEMS; ++it) {
         const int pos = wbase + it * 32 + lane;
         if (pos < n) {
             const K k = kin[pos];
@@ -136,23 +136,35 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
 
 // Sort keys[0] / vals[0] (n entries) over the digits at `shifts`; buffers
 // keys[1] / vals[1] are ping-pong space; *out receives the index of the
-// buffer pair holding the result.  hist: kSortBins * ceil(n / kSortTile)
+// buffer pair holding the result.  Tiles hold 1024 keys below 2^18 keys (more
+// blocks for small sorts), 4096 above.  hist: kSortBins * ceil(n / 1024)
 // words, totals: kSortBins words.
-template <typename K>
-cudaError_t radix_sort(K* keys[2], uint32_t* vals[2], int n, const int* shifts, int np,
-                       uint32_t* hist, uint32_t* totals, cudaStream_t s, int* out) {
-    const int ntiles = (n + kSortTile - 1) / kSortTile;
+template <typename K, int ITEMS>
+static cudaError_t radix_sort_tiles(K* keys[2], uint32_t* vals[2], int n, const int* shifts,
+                                    int np, uint32_t* hist, uint32_t* totals, cudaStream_t s,
+                                    int* out) {
+    const int tile = kSortThreads * ITEMS;
+    const int ntiles = (n + tile - 1) / tile;
     int cur = 0;
     for (int p = 0; p < np && n > 0; ++p) {
-        k_sort_hist<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], n, shifts[p], hist, ntiles);
+        k_sort_hist<K, ITEMS><<<ntiles, kSortThreads, 0, s>>>(keys[cur], n, shifts[p], hist,
+                                                              ntiles);
         k_sort_scan<<<kSortBins, 256, 0, s>>>(hist, ntiles, totals);
-        k_sort_scatter<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[1 - cur],
-                                                          vals[1 - cur], n, shifts[p], hist,
-                                                          totals, ntiles);
+        k_sort_scatter<K, ITEMS><<<ntiles, kSortThreads, 0, s>>>(
+            keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], n, shifts[p], hist, totals,
+            ntiles);
         cur = 1 - cur;
     }
     *out = cur;
     return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t radix_sort(K* keys[2], uint32_t* vals[2], int n, const int* shifts, int np,
+                       uint32_t* hist, uint32_t* totals, cudaStream_t s, int* out) {
+    if (n < (1 << 18))
+        return radix_sort_tiles<K, 4>(keys, vals, n, shifts, np, hist, totals, s, out);
+    return radix_sort_tiles<K, kSortItems>(keys, vals, n, shifts, np, hist, totals, s, out);
 }
 
 }  // namespace rsi
