@@ -372,6 +372,53 @@ static __device__ __noinline__ int mt64(float ax_, float ay_, float az_, float b
     return hit;
 }
 
+// A tighter rigorous bound on the FP32 (t, u, v) of one (segment,
+// triangle) pair, for the nearest crossing's outputs: the same triple
+// products as mt32, but the rounding error of each is bounded with the
+// componentwise magnitudes sum |x_i| (|y_j| |z_k| + |y_k| |z_j|) and gamma_10
+// (every term carries at most 8 roundings, 2 more cover the magnitudes'
+// own rounding), instead of the max-norm products and 2^-17 that decisions
+// use.  Returns the bound on max(|t~ - t|, |u~ - u|, |v~ - v|) and the FP32
+// values; +inf when det cannot be bounded away from zero.
+__device__ __forceinline__ float mt32_tight(const Seg& s, const float4& A, const float4& B,
+                                           const float4& C, float& t, float& u, float& v) {
+    const float e1x = B.x - A.x, e1y = B.y - A.y, e1z = B.z - A.z;
+    const float e2x = C.x - A.x, e2y = C.y - A.y, e2z = C.z - A.z;
+    const float sx = s.ax - A.x, sy = s.ay - A.y, sz = s.az - A.z;
+    const float px = s.dy * e2z - s.dz * e2y, py = s.dz * e2x - s.dx * e2z;
+    const float pz = s.dx * e2y - s.dy * e2x;
+    const float qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;
+    const float det = e1x * px + e1y * py + e1z * pz;
+    const float nu = sx * px + sy * py + sz * pz;
+    const float nv = s.dx * qx + s.dy * qy + s.dz * qz;
+    const float nt = e2x * qx + e2y * qy + e2z * qz;
+    // componentwise magnitudes of p and q
+    const float Px = fabsf(s.dy) * fabsf(e2z) + fabsf(s.dz) * fabsf(e2y);
+    const float Py = fabsf(s.dz) * fabsf(e2x) + fabsf(s.dx) * fabsf(e2z);
+    const float Pz = fabsf(s.dx) * fabsf(e2y) + fabsf(s.dy) * fabsf(e2x);
+    const float Qx = fabsf(sy) * fabsf(e1z) + fabsf(sz) * fabsf(e1y);
+    const float Qy = fabsf(sz) * fabsf(e1x) + fabsf(sx) * fabsf(e1z);
+    const float Qz = fabsf(sx) * fabsf(e1y) + fabsf(sy) * fabsf(e1x);
+    const float g = 10.f * 0x1p-24f * 1.0001f;
+    const float Bd = g * (fabsf(e1x) * Px + fabsf(e1y) * Py + fabsf(e1z) * Pz) + kFilterEta;
+    const float Bu = g * (fabsf(sx) * Px + fabsf(sy) * Py + fabsf(sz) * Pz) + kFilterEta;
+    const float Bv = g * (fabsf(s.dx) * Qx + fabsf(s.dy) * Qy + fabsf(s.dz) * Qz) + kFilterEta;
+    const float Bt = g * (fabsf(e2x) * Qx + fabsf(e2y) * Qy + fabsf(e2z) * Qz) + kFilterEta;
+    const float ad = fabsf(det);
+    if (!(ad > 2.f * Bd) || !isfinite(ad)) return INFINITY;
+    const float inv = __frcp_rn(ad);
+    const float sg = det < 0.f ? -1.f : 1.f;
+    t = sg * nt * inv;
+    u = sg * nu * inv;
+    v = sg * nv * inv;
+    // |x/det~ - x_exact/det_exact| <= (B_x + |x| B_det / |det|) / (|det| - B_det) + rounding
+    const float den = __frcp_rn(ad - Bd);
+    const float et = fmaf(fabsf(t), Bd, Bt) * den;
+    const float eu = fmaf(fabsf(u), Bd, Bu) * den;
+    const float ev = fmaf(fabsf(v), Bd, Bv) * den;
+    return fmaxf(fmaxf(et, eu), ev) * 1.001f + 0x1p-22f * fmaxf(1.f, fmaxf(fabsf(t), fmaxf(fabsf(u), fabsf(v))));
+}
+
 // ---------------------------------------------------------------- double-float
 // Unevaluated sums h + l of two floats (about 44 significant bits) built from
 // the error-free transformations two-sum (Knuth) and two-product (via FMA),
@@ -409,10 +456,12 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
     return df_fast(p, e);
 }
 
-__device__ __forceinline__ dfl df_div(dfl a, dfl b) {
-    const float q1 = __fdiv_rn(a.h, b.h);
-    const dfl r = df_add(a, df_neg(df_mul(b, {q1, 0.f})));
-    const float q2 = __fdiv_rn(r.h, b.h);
+// a / b given r ~ 1 / b.h (any 1-ulp approximation): q1 = a.h r, then one
+// correction from the exact double-float residual a - b q1.
+__device__ __forceinline__ dfl df_div(dfl a, dfl b, float r) {
+    const float q1 = __fmul_rn(a.h, r);
+    const dfl res = df_add(a, df_neg(df_mul(b, {q1, 0.f})));
+    const float q2 = __fmul_rn(res.h, r);
     return df_fast(q1, q2);
 }
 
@@ -444,9 +493,10 @@ static __device__ __noinline__ void mt_df(const float* a3, const float* b3, floa
     const dfl det = dot(e1, p);
     cross(s0, e1, q);
     const dfl nu = dot(s0, p), nv = dot(d, q), nt = dot(e2, q);
-    tuv[0] = df_float(df_div(nt, det));
-    tuv[1] = df_float(df_div(nu, det));
-    tuv[2] = df_float(df_div(nv, det));
+    const float r = rcp_approx(det.h);
+    tuv[0] = df_float(df_div(nt, det, r));
+    tuv[1] = df_float(df_div(nu, det, r));
+    tuv[2] = df_float(df_div(nv, det, r));
 }
 
 }  // namespace rsi

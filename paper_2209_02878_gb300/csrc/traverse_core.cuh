@@ -318,10 +318,11 @@ __device__ __forceinline__ void result_init(Result& r) {
     r.b64 = false;
 }
 
-// Nearest outputs; (t, u, v) are recomputed in double-float when their FP32
-// error bound could move the point by more than about 2^-21 (the sign of a
-// sign-normalised det cannot change there: the hit was already decided), and
-// in FP64 for segments whose direction is outside the FP32 filter's range.
+// Nearest outputs.  (t, u, v) keep their FP32 values when a rigorous bound
+// (first the filter's, then a tighter one for this triangle) shows them, and
+// the point, within half the 1e-5 tolerance; otherwise they are recomputed in
+// double-float, and in FP64 for segments whose direction is outside the FP32
+// filter's range.
 template <bool STATS>
 __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, const float* B,
                                                int64_t i, const float4* __restrict__ tris,
@@ -330,7 +331,10 @@ __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, con
     t = res.bt;
     u = res.bu;
     v = res.bv;
-    const float thresh = 0x1p-21f / fmaxf(1.f, s.md * 1.7320508f);
+    // the tolerance of these outputs is 1e-5 (of the point too, which moves by
+    // |d| times the error of t); the bounds are rigorous, keep a margin of 2
+    const float dlen = sqrtf(fmaf(s.dx, s.dx, fmaf(s.dy, s.dy, s.dz * s.dz))) * 1.0001f;
+    const float thresh = 5e-6f / fmaxf(1.f, dlen);
     const int p = res.bpos;
     if (s.fp64only) {
         if (STATS) ++st.refines;
@@ -350,7 +354,19 @@ __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, con
         dist = (float)(tuv[0] * sqrt(dd));
         return;
     }
-    if (res.berr > thresh) {
+    bool refine = res.berr > thresh;
+    if (refine) {  // a tighter bound for this one triangle first
+        float t2, u2, v2;
+        const float e = mt32_tight(s, ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
+                                   ld4(tris + 3 * (int64_t)p + 2), t2, u2, v2);
+        if (e <= thresh) {
+            t = t2;
+            u = u2;
+            v = v2;
+            refine = false;
+        }
+    }
+    if (refine) {
         if (STATS) ++st.refines;
         const float a3[3] = {s.ax, s.ay, s.az};
         const float b3[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
