@@ -12,8 +12,11 @@
 
 namespace rsi {
 
+// All three modes are inlined into one kernel; without a cap it needs ~170
+// registers (two warps per scheduler), with it the spills stay in the cold
+// paths.
 template <int STACK>
-__global__ void k_batch(BatchParams P) {
+__global__ void __maxnreg__(72) k_batch(BatchParams P) {
     TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull};
     unsigned long long segs = 0;
     const int lane = threadIdx.x & 31;
