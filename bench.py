@@ -39,7 +39,10 @@ BYTES_PER_SEG_COUNT = 28
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace<BOOL> launch on
 # this workload (ncu, profiles/k_trace_bool_paper_scale.md), valid while the
 # traversal sources hash to `sha`; otherwise reported as null
-TRAFFIC = {"sha": "cf9700a15165dc94", "bytes": 259_822_848}
+TRAFFIC = {"sha": "cf9700a15165dc94", "bytes": 259_822_848, "warp_inst": 1_144_566_821}
+# peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle at
+# the maximum SM clock (2,070 MHz)
+ISSUE_PEAK = 152 * 4 * 2.070e9
 TRAVERSAL_SOURCES = ("traverse_core.cuh", "rsi_internal.cuh", "traverse.cu")
 
 
@@ -277,6 +280,11 @@ def run_ours(args):
                      "traffic": TRAFFIC["bytes"] if traversal_sha() == TRAFFIC["sha"] else None,
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "kernel_ms": round(ms_trav, 4)},
+        "issue_roofline": ({"bound": "issue", "kernel": "k_trace<BOOL>",
+                            "achieved": round(TRAFFIC["warp_inst"] / (ms_trav * 1e-3) / 1e12, 4),
+                            "peak": round(ISSUE_PEAK / 1e12, 4), "unit": "Twarp-inst/s",
+                            "frac": round(TRAFFIC["warp_inst"] / (ms_trav * 1e-3) / ISSUE_PEAK, 4)}
+                           if traversal_sha() == TRAFFIC["sha"] else None),
         "breakdown": {"traverse_only_Msegs": round(n_seg / (ms_trav * 1e-3) / 1e6, 3),
                       "build_ms": round(ms_build, 4), "traverse_ms": round(ms_trav, 4),
                       "node_visits_per_seg": round(stats["node_visits"] / n_seg, 3),
@@ -353,7 +361,11 @@ def run_extras(args, torch, rsi, synth, dev, stream):
                  torch.from_numpy(s.A).to(dev), torch.from_numpy(s.B).to(dev), mode)
                 for m, s, mode in items]
         n_total = sum(s.n for _, s, _ in items)
-        batch = rsi.Batch(tens, stream=stream)
+        from paper_2209_02878_gb300 import tuning
+        # block size, stack depth and leaf size from the project's autotuner
+        # (timed outside the measured region; cached per GPU / workload class)
+        tuned, leaf, _ = tuning.autotune_batch(tens, cache=None, stream=stream)
+        batch = rsi.Batch(tens, leaf_size=leaf, launch=tuned, stream=stream)
         batch.run_graph(rebuild=True, stream=stream)
         stream.synchronize()
         ms_bt = timed(lambda: batch.run_graph(rebuild=True, stream=stream), steps, stream, torch)
@@ -371,6 +383,7 @@ def run_extras(args, torch, rsi, synth, dev, stream):
                                       "bool/nearest alternating, one graph: build + persistent "
                                       "traversal",
                           "value": round(n_total / (ms_bt * 1e-3) / 1e6, 3), "unit": UNIT,
+                          "autotuned": dict(tuned, leaf_size=leaf),
                           "per_mesh_launches": round(n_total / (ms_single * 1e-3) / 1e6, 3)}
         batch.close()
     return out

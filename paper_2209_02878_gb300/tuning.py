@@ -79,3 +79,51 @@ def autotune(bvh, V, T, A, B, mode="bool", block_sizes=(64, 128, 256, 512),
         with open(cache, "w") as f:
             json.dump(data, f, indent=1)
     return launch, best_leaf.value, rows
+
+
+def autotune_batch(items, block_sizes=(64, 128, 256), stack_depths=(32, 64),
+                   leaf_sizes=(1, 2, 4), reps=3, cache: str | None = DEFAULT_CACHE,
+                   stream=None):
+    """Tune the batched launch: for each leaf size (a multi-mesh build) and
+    launch configuration, time `reps` persistent traversals of the whole batch
+    with CUDA events and return (best launch dict, best leaf size, table).
+    `items` as for Batch: (V, T, A, B, mode) tuples of CUDA tensors."""
+    from . import Batch
+    n_tri = sum(int(t[1].shape[0]) for t in items)
+    n_seg = sum(int(t[2].shape[0]) for t in items)
+    key = cache_key("batch%d" % len(items), n_tri, n_seg, items[0][0].device)
+    if cache:
+        hit = _load(cache).get(key)
+        if hit:
+            return hit["launch"], hit["leaf_size"], hit.get("table", [])
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rows = []
+    with torch.cuda.stream(s):
+        for leaf in leaf_sizes:
+            for bs in block_sizes:
+                for sd in stack_depths:
+                    launch = dict(block_size=bs, stack_depth=sd)
+                    b = Batch(items, leaf_size=leaf, launch=launch, stream=s)
+                    b.build(stream=s)
+                    b.intersect(stream=s)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    ms = []
+                    for _ in range(reps):
+                        e0.record(s)
+                        b.intersect(stream=s)
+                        e1.record(s)
+                        e1.synchronize()
+                        ms.append(e0.elapsed_time(e1))
+                    b.close()
+                    rows.append(dict(block_size=bs, stack_depth=sd, leaf_size=leaf,
+                                     ms=sorted(ms)[len(ms) // 2]))
+    best = min(rows, key=lambda r: r["ms"])
+    launch = dict(block_size=best["block_size"], stack_depth=best["stack_depth"])
+    if cache:
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        data = _load(cache)
+        data[key] = dict(launch=launch, leaf_size=best["leaf_size"], table=rows)
+        with open(cache, "w") as f:
+            json.dump(data, f, indent=1)
+    return launch, best["leaf_size"], rows
