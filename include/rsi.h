@@ -257,7 +257,7 @@ rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR
 /* rsi_intersect from HOST buffers: hA, hB float[nR][3] and the outputs in
  * *hout (flag / count / tri, tuv, point, dist as for rsi_intersect) are host
  * pointers; compaction (hout->hit_idx) is not supported.  The segments go
- * through in chunks of `chunk` (0 -> 2^20) on two internal streams with
+ * through in chunks of `chunk` (0 -> 2^21) on two internal streams with
  * double-buffered device staging (56 B per segment per buffer, allocated by
  * the handle on first use, cudaMallocAsync on s), so that the copy of one
  * chunk to the device, the traversal of the previous one and the copy of

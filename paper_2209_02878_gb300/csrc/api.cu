@@ -29,7 +29,7 @@ namespace {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr int kDefaultBlock = 128;
-constexpr int64_t kHostChunk = (int64_t)1 << 20;  // segments per pipeline chunk
+constexpr int64_t kHostChunk = (int64_t)1 << 21;  // segments per pipeline chunk
 
 // Carves the device buffers of a tree over N triangles and M meshes out of
 // one allocation.  With base == nullptr only the total size is computed.
