@@ -39,7 +39,7 @@ BYTES_PER_SEG_COUNT = 28
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace<BOOL> launch on
 # this workload (ncu, profiles/k_trace_bool_paper_scale.md), valid while the
 # traversal sources hash to `sha`; otherwise reported as null
-TRAFFIC = {"sha": "453ef5d0324888fa", "bytes": 259_944_960, "warp_inst": 1_144_736_439}
+TRAFFIC = {"sha": "cb9cfbc2756ecf23", "bytes": 260_059_648, "warp_inst": 1_002_803_441}
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle at
 # the maximum SM clock (2,070 MHz)
 ISSUE_PEAK = 152 * 4 * 2.070e9

@@ -55,13 +55,17 @@ static __device__ __noinline__ double exact_t(const float* A, const float* B, in
     return tuv[0];
 }
 
-// Test the cnt triangles of a leaf.  Returns true when BOOL found a crossing.
+// Test the triangles at leaf positions [first, first + cnt) and then
+// [first1, first1 + cnt1) in one loop (so lanes whose leaf is either child of
+// a node test together).  Returns true when BOOL found a crossing.
 template <int MODE, bool STATS>
 __device__ __forceinline__ bool leaf_test(const Seg& s, const float* A, const float* B, int64_t i,
                                           const float4* __restrict__ tris, int first, int cnt,
-                                          Result& res, float& tlim, TravStats& st) {
-    for (int k = 0; k < cnt; ++k) {
-        const int pos = first + k;
+                                          int first1, int cnt1, Result& res, float& tlim,
+                                          TravStats& st) {
+    const int tot = cnt + cnt1;
+    for (int k = 0; k < tot; ++k) {
+        const int pos = k < cnt ? first + k : first1 + (k - cnt);
         const float4 a = ld4(tris + 3 * (int64_t)pos);
         const float4 b = ld4(tris + 3 * (int64_t)pos + 1);
         const float4 c = ld4(tris + 3 * (int64_t)pos + 2);
@@ -186,10 +190,19 @@ __device__ __forceinline__ bool node_step(const TraceCtx& C, const Seg& s, int64
     bool h0, h1;
     slab2(s, q0, q1, q2, tlim, h0, t0, h1, t1);
     const int r0 = rc.x, r1 = rc.y, c0 = rc.z, c1 = rc.w;
-    if (h0 && c0 > 0 && leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r0, c0, res, tlim, st))
-        return true;
-    if (h1 && c1 > 0 && leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r1, c1, res, tlim, st))
-        return true;
+    // one loop over both leaves for BOOL and COUNT; NEAREST keeps two (its
+    // merged loop measured slower: more live state across the loop)
+    if (MODE == RSI_MODE_NEAREST) {
+        if (h0 && c0 > 0)
+            leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r0, c0, 0, 0, res, tlim, st);
+        if (h1 && c1 > 0)
+            leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r1, c1, 0, 0, res, tlim, st);
+    } else {
+        const int n0 = h0 && c0 > 0 ? c0 : 0, n1 = h1 && c1 > 0 ? c1 : 0;
+        if ((n0 | n1) &&
+            leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r0, n0, r1, n1, res, tlim, st))
+            return true;
+    }
     const bool g0 = h0 && c0 <= 0, g1 = h1 && c1 <= 0;
     const int x0 = c0 < 0 ? ~r0 : r0, x1 = c1 < 0 ? ~r1 : r1;
     if (g0 && g1) {
@@ -251,7 +264,7 @@ __device__ __forceinline__ bool node_step4(const TraceCtx& C, const Seg& s, int6
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         if (h[q] && c[q] > 0 &&
-            leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r[q], c[q], res, tlim, st))
+            leaf_test<MODE, STATS>(s, C.A, C.B, i, C.tris, r[q], c[q], 0, 0, res, tlim, st))
             return true;
     // internal children, sorted by entry parameter (misses keyed +inf)
     float k0 = (h[0] && c[0] == 0) ? t[0] : INFINITY, k1 = (h[1] && c[1] == 0) ? t[1] : INFINITY;
@@ -442,11 +455,15 @@ __device__ __forceinline__ void compact(const TravOut& o, bool has, int64_t i, c
 }
 
 constexpr int kFetchChunk = 128;  // segments a warp takes from the global counter at once
+constexpr int kRefillMin = 8;     // idle lanes that trigger a refill of a busy warp
 
 // Persistent per-warp traversal loop over segments [lo, hi).  Every lane
-// holds one segment and advances it by one node per iteration; a lane whose
-// segment finishes takes the next one from the warp's pool right away, so the
-// warp does not idle behind its slowest lane.  The pool is refilled with
+// holds one segment and advances it by one node per iteration; lanes whose
+// segments finish take the next ones from the warp's pool as soon as
+// kRefillMin of them are free, so the warp does not idle behind its slowest
+// lane and the divergent segment setup runs for several lanes at once.  A
+// finished lane keeps its result until that refill and writes it then,
+// together with the other finished lanes.  The pool is refilled with
 // kFetchChunk segments from *counter (one atomic per chunk), or, with
 // counter == nullptr, holds the whole range [lo, hi) from the start.  When
 // `order` is given, pool position k processes segment order[k] (a coherent
@@ -469,8 +486,24 @@ __device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long
     Result res;
     result_init(res);
     int stack[STACK];
+    bool done = false;  // segment i finished, its outputs not yet written
     while (true) {
-        unsigned idle = __ballot_sync(FULL, i < 0);
+        unsigned idle = __ballot_sync(FULL, i < 0 || done);
+        // Refill in batches: the setup of a new segment and the writes of a
+        // finished one run divergently, so wait until kRefillMin lanes are
+        // free (or the whole warp is).
+        if (__popc(idle) < kRefillMin && idle != FULL) idle = 0u;
+        if (idle) {  // outputs of the finished segments first
+            float dist = 0.f, P[3] = {0.f, 0.f, 0.f};
+            if (done)
+                write_result<MODE, STATS>(C.out, s, true, C.A, C.B, i, C.tris, res, dist, P, st);
+            if (MODE != RSI_MODE_BOOL && C.out.hit_idx)
+                compact<MODE>(C.out, done && res.count > 0, i, res, dist, P);
+            if (done) {
+                i = -1;
+                done = false;
+            }
+        }
         while (idle) {
             if (pool >= pool_end) {
                 if (!more) break;
@@ -507,29 +540,19 @@ __device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long
             idle = __ballot_sync(FULL, i < 0);
         }
         if (__ballot_sync(FULL, i >= 0) == 0u) break;
-        bool fin = false;
-        float dist = 0.f, P[3] = {0.f, 0.f, 0.f};
-        if (i >= 0) {
+        if (i >= 0 && !done) {
             bool overflow = false;
             if (W == 4)
-                fin = node_step4<MODE, STACK, STATS>(C, s, i, node, sp, stack, tlim, res, visits,
-                                                     overflow, st);
+                done = node_step4<MODE, STACK, STATS>(C, s, i, node, sp, stack, tlim, res, visits,
+                                                      overflow, st);
             else
-                fin = node_step<MODE, STACK, STATS>(C, s, i, node, sp, stack, tlim, res, visits,
-                                                    overflow, st);
-            if (fin) {
-                // a binary traversal needs at most 63 entries; a 4-wide one may
-                // push up to 3 per level and re-runs in binary on overflow
-                if ((STACK < 64 || W == 4) && overflow) {
-                    if (STATS) ++st.overflows;
-                    trace_deep<MODE, STATS>(C, s, i, res, st);
-                }
-                write_result<MODE, STATS>(C.out, s, true, C.A, C.B, i, C.tris, res, dist, P, st);
+                done = node_step<MODE, STACK, STATS>(C, s, i, node, sp, stack, tlim, res, visits,
+                                                     overflow, st);
+            if (done && (STACK < 64 || W == 4) && overflow) {
+                if (STATS) ++st.overflows;
+                trace_deep<MODE, STATS>(C, s, i, res, st);
             }
         }
-        if (MODE != RSI_MODE_BOOL && C.out.hit_idx)
-            compact<MODE>(C.out, fin && res.count > 0, i, res, dist, P);
-        if (fin) i = -1;
     }
 }
 
