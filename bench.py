@@ -39,7 +39,7 @@ BYTES_PER_SEG_COUNT = 28
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace<BOOL> launch on
 # this workload (ncu, profiles/k_trace_bool_paper_scale.md), valid while the
 # traversal sources hash to `sha`; otherwise reported as null
-TRAFFIC = {"sha": "cb9cfbc2756ecf23", "bytes": 260_059_648, "warp_inst": 1_002_803_441}
+TRAFFIC = {"sha": "522d87f7cb0633c4", "bytes": 260_353_280, "warp_inst": 996_032_860}
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle at
 # the maximum SM clock (2,070 MHz)
 ISSUE_PEAK = 152 * 4 * 2.070e9

@@ -13,10 +13,11 @@
 namespace rsi {
 
 // All three modes are inlined into one kernel; without a cap it needs ~170
-// registers (two warps per scheduler), with it the spills stay in the cold
-// paths.
+// registers (two warps per scheduler).  128 measured fastest on the 64-mesh
+// mix (8.37 ms against 8.79 ms at 96 and 9.52 ms at 72, where the nearest
+// path spills).
 template <int STACK>
-__global__ void __maxnreg__(72) k_batch(BatchParams P) {
+__global__ void __maxnreg__(128) k_batch(BatchParams P) {
     TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull};
     unsigned long long segs = 0;
     const int lane = threadIdx.x & 31;

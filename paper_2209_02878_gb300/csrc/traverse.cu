@@ -1,8 +1,8 @@
 // Single-mesh traversal launch (arXiv 2209.02878, Sec. 3.3
 // bvhIntersectionKernel): a persistent grid sized from the occupancy query
 // (the paper's N_grid lesson, Sec. 3.3: fill the machine), each warp pulling
-// 32 segments at a time from an atomic counter, the top treelet staged once
-// per block in shared memory.
+// kFetchChunk segments at a time from an atomic counter, optionally the top
+// treelet staged once per block in shared memory.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -12,11 +12,12 @@
 
 namespace rsi {
 
-// Register caps per mode (measured on the paper-scale workload: fewer
-// registers, more resident warps to hide the dependent node fetches).
+// Register caps per mode, measured on the paper-scale workload: BOOL gains
+// more from resident warps (hiding the dependent node fetches) than it loses
+// to a few spills; NEAREST carries more state and spills badly below 80.
 template <int MODE>
 struct TraceRegs {
-    static constexpr int value = MODE == RSI_MODE_BOOL ? 64 : 72;
+    static constexpr int value = MODE == RSI_MODE_BOOL ? 64 : (MODE == RSI_MODE_COUNT ? 72 : 80);
 };
 
 template <int MODE, int STACK, bool STATS, int W>

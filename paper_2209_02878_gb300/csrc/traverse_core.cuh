@@ -130,6 +130,23 @@ __device__ __forceinline__ bool leaf_test(const Seg& s, const float* A, const fl
     return false;
 }
 
+// One 64 B node record in two 256-bit read-only loads (the record is 64 B
+// aligned).
+__device__ __forceinline__ void ld_node(const float4* rec, ulonglong2& q0, ulonglong2& q1,
+                                        ulonglong2& q2, int4& rc) {
+    unsigned long long r0, r1;
+    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(q0.x), "=l"(q0.y), "=l"(q1.x), "=l"(q1.y)
+        : "l"(rec));
+    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(q2.x), "=l"(q2.y), "=l"(r0), "=l"(r1)
+        : "l"(rec + 2));
+    rc.x = (int)(unsigned)r0;
+    rc.y = (int)(unsigned)(r0 >> 32);
+    rc.z = (int)(unsigned)r1;
+    rc.w = (int)(unsigned)(r1 >> 32);
+}
+
 // Everything one traversal launch needs (by value in registers / params).
 struct TraceCtx {
     const float* A;
@@ -172,18 +189,10 @@ __device__ __forceinline__ bool node_step(const TraceCtx& C, const Seg& s, int64
             q2 = p[2];
             rc = ((const int4*)p)[3];
         } else {
-            const ulonglong2* p = (const ulonglong2*)(C.treelet + 4 * (int64_t)k);
-            q0 = __ldg(p);
-            q1 = __ldg(p + 1);
-            q2 = __ldg(p + 2);
-            rc = __ldg((const int4*)p + 3);
+            ld_node(C.treelet + 4 * (int64_t)k, q0, q1, q2, rc);
         }
     } else {
-        const ulonglong2* p = (const ulonglong2*)(C.nodes + 4 * (int64_t)node);
-        q0 = __ldg(p);
-        q1 = __ldg(p + 1);
-        q2 = __ldg(p + 2);
-        rc = __ldg((const int4*)p + 3);
+        ld_node(C.nodes + 4 * (int64_t)node, q0, q1, q2, rc);
     }
     if (STATS) ++st.visits;
     float t0, t1;
