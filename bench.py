@@ -233,8 +233,9 @@ def run_ours(args):
         stats = bvh.intersect(A, B, "bool", stats=True, stream=stream)["stats"]
 
         # end to end through the public API from pinned host memory: the
-        # build plus rsi_intersect_host (chunked, copies overlapped with the
-        # traversal on two internal streams) every step
+        # build plus rsi_intersect_host every step (the kernel reads the
+        # pinned segments in place over the CPU-GPU link, the flags come back
+        # with one device-to-host copy)
         hA = torch.from_numpy(seg.A).pin_memory()
         hB = torch.from_numpy(seg.B).pin_memory()
         hout = {"flag": torch.empty(n_seg, dtype=torch.uint8).pin_memory()}

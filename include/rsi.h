@@ -259,12 +259,16 @@ rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR
  * pointers; compaction (hout->hit_idx) is not supported.  The segments go
  * through in chunks of `chunk` (0 -> 2^21) on two internal streams with
  * double-buffered device staging (56 B per segment per buffer, allocated by
- * the handle on first use, cudaMallocAsync on s), so that the copy of one
- * chunk to the device, the traversal of the previous one and the copy of
- * results back overlap.  The work is ordered after everything already on s,
- * and s waits for it: the host outputs are complete once s is synchronised.
- * With pageable host memory the copies are staged by the driver and overlap
- * less; pinned memory gives full overlap.  Segments are processed in input
+ * the handle on first use, cudaMallocAsync on s), so that the traversal of
+ * one chunk and the copy of the previous chunk's results back overlap.
+ * When hA and hB both lie in page-locked memory the device can address
+ * (cudaHostAlloc / cudaHostRegister, unified addressing), the traversal
+ * kernel reads the segments in place over the CPU-GPU link; otherwise each
+ * chunk is first copied to the staging buffer, overlapped with the previous
+ * chunk's traversal.  The work is ordered after everything already on s,
+ * and s waits for it: the host outputs are complete once s is synchronised
+ * (hA and hB must stay unchanged until then).  Pageable host memory is
+ * staged by the driver and overlaps less.  Segments are processed in input
  * order (lo->sort_bits is ignored).  Errors as rsi_intersect, plus
  * RSI_ERR_OOM. */
 rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64_t nR,

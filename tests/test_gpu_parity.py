@@ -251,14 +251,26 @@ def test_refit_moves_with_vertices(small):
     tree_check(bvh.export(), mesh.n_tri)
 
 
-@pytest.mark.parametrize("chunk,pin", [(0, True), (1000, True), (4103, False), (10**9, True)])
+@pytest.mark.parametrize("chunk,pin", [(0, "both"), (1000, "both"), (4103, "none"),
+                                       (10**9, "both"), (777, "A only"), (0, "offset")])
 def test_intersect_from_host_buffers(small, chunk, pin):
+    """Both host paths: page-locked inputs read in place by the kernel
+    ("both", and "offset": views starting inside a pinned allocation) and
+    inputs staged by copies ("none", and "A only", where one of the two
+    arrays is pageable)."""
     mesh, seg, ref = small
     bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
     A = torch.from_numpy(seg.A)
     B = torch.from_numpy(seg.B)
-    if pin:
+    if pin == "both":
         A, B = A.pin_memory(), B.pin_memory()
+    elif pin == "A only":
+        A = A.pin_memory()
+    elif pin == "offset":
+        k = 5
+        A = torch.cat([torch.zeros(k, 3), A]).pin_memory()[k:]
+        B = torch.cat([torch.zeros(k, 3), B]).pin_memory()[k:]
+        assert A.is_contiguous() and A.is_pinned()
     s = torch.cuda.Stream()
     got = {}
     for m in ("bool", "count", "nearest"):
