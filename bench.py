@@ -43,6 +43,12 @@ TRAFFIC = {"sha": "522d87f7cb0633c4", "bytes": 260_353_280, "warp_inst": 996_032
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle at
 # the maximum SM clock (2,070 MHz)
 ISSUE_PEAK = 152 * 4 * 2.070e9
+# FP32 operations the traversal performs per node visit (two child boxes, each
+# 6 subtract + 6 multiply + 4 max + 4 min + 1 multiply + 1 compare... counted
+# as 20) and per Moller-Trumbore test (~50); compared with the FP32 rate that
+# rsi_fp32_peak measures on the same GPU
+FP32_OPS_PER_VISIT = 40
+FP32_OPS_PER_TEST = 50
 TRAVERSAL_SOURCES = ("traverse_core.cuh", "rsi_internal.cuh", "traverse.cu")
 
 
@@ -144,6 +150,17 @@ def timed(fn, steps, stream, torch):
     return e0.elapsed_time(e1) / steps
 
 
+def cpu_oracle_1thread(mesh, seg, n=200_000):
+    """The same oracle on one host thread, on the first n segments.
+    Returns (Mseg/s, n, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    bvh = oracle.CpuBVH(mesh.V, mesh.T)
+    bvh.query(seg.A[:n], seg.B[:n], threads=1)
+    dt = time.perf_counter() - t0
+    return n / dt / 1e6, n, dt
+
+
 def cpu_oracle_rate(mesh, seg, target_s=12.0, max_n=10_000_000):
     """The FP64 oracle (CPU BVH + Moller-Trumbore, OpenMP over all host
     cores) on a bounded sample of the segments: build + query.
@@ -231,6 +248,8 @@ def run_ours(args):
                         args.steps, stream, torch)
         ms_build = timed(lambda: bvh.build(V, T, stream=stream), args.steps, stream, torch)
         stats = bvh.intersect(A, B, "bool", stats=True, stream=stream)["stats"]
+        # the FP32 ceiling, measured by the library's FMA probe (~60 ms)
+        fp32_tflops = rsi.fp32_peak(1 << 20, stream=stream)
 
         # end to end through the public API from pinned host memory: the
         # build plus rsi_intersect_host every step (the kernel reads the
@@ -257,6 +276,8 @@ def run_ours(args):
 
     peak, peak_kind = measured_peaks()
     algo_bytes = BYTES_PER_SEG_BOOL * n_seg
+    fp32_ops = (FP32_OPS_PER_VISIT * stats["node_visits"] +
+                FP32_OPS_PER_TEST * stats["tri_tests"])
     achieved = algo_bytes / (ms_trav * 1e-3) / 1e9
     res = {
         "metric": METRIC, "value": round(world * n_seg / (ms_step * 1e-3) / 1e6, 3),
@@ -286,6 +307,13 @@ def run_ours(args):
                             "peak": round(ISSUE_PEAK / 1e12, 4), "unit": "Twarp-inst/s",
                             "frac": round(TRAFFIC["warp_inst"] / (ms_trav * 1e-3) / ISSUE_PEAK, 4)}
                            if traversal_sha() == TRAFFIC["sha"] else None),
+        "fp32_roofline": {"bound": "fp32", "kernel": "k_trace<BOOL>",
+                          "achieved": round(fp32_ops / (ms_trav * 1e-3) / 1e12, 4),
+                          "peak": round(fp32_tflops, 3), "unit": "TFLOP/s",
+                          "frac": round(fp32_ops / (ms_trav * 1e-3) / 1e12 / fp32_tflops, 5),
+                          "peak_kind": "measured (rsi_fp32_peak FMA probe)",
+                          "ops_per_visit": FP32_OPS_PER_VISIT,
+                          "ops_per_test": FP32_OPS_PER_TEST},
         "breakdown": {"traverse_only_Msegs": round(n_seg / (ms_trav * 1e-3) / 1e6, 3),
                       "build_ms": round(ms_build, 4), "traverse_ms": round(ms_trav, 4),
                       "node_visits_per_seg": round(stats["node_visits"] / n_seg, 3),
@@ -295,10 +323,13 @@ def run_ours(args):
     res.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, thr, n, dt = cpu_oracle_rate(mesh, seg)
+        rate1, n1, dt1 = cpu_oracle_1thread(mesh, seg)
         res["cpu_baseline"] = {"value": round(rate, 5), "unit": UNIT, "cores": thr,
                                "kind": "oracle",
                                "sample": f"first {n} of the 10M segments, CPU BVH build + "
-                                         f"FP64 query, {dt:.1f} s"}
+                                         f"FP64 query, {dt:.1f} s",
+                               "one_thread": {"value": round(rate1, 5),
+                                              "sample": f"first {n1} segments, {dt1:.1f} s"}}
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -308,8 +339,9 @@ def run_ours(args):
 
 def run_extras(args, torch, rsi, synth, dev, stream):
     """fwd+bwd (131k-triangle heightfield, 262k segments), count + nearest
-    (1.3M-triangle icosphere, 1M segments) and the 64-mesh batch, each beside
-    the plain single-mesh forward on the same mesh."""
+    (1.3M-triangle icosphere, 1M segments), a coherent raster of segments
+    (per-segment stacks against warp packets) and the 64-mesh batch, each
+    beside the plain single-mesh forward on the same mesh."""
     out = {}
     steps = max(3, args.steps)
     with torch.cuda.stream(stream):
@@ -356,6 +388,24 @@ def run_extras(args, torch, rsi, synth, dev, stream):
         out["sphere"] = {"workload": "icosphere L8 (1,310,720 tris) x 1M segments in a cube",
                          "traverse_Msegs": res, "build_ms": round(ms_b, 3), "unit": UNIT}
         del bvh
+        # coherent segments: one stack per segment against warp packets
+        mesh, seg = synth.workload_raster()
+        V = torch.from_numpy(mesh.V).to(dev)
+        T = torch.from_numpy(mesh.T).to(dev)
+        A = torch.from_numpy(seg.A).to(dev)
+        B = torch.from_numpy(seg.B).to(dev)
+        bvh = rsi.BVH(V, T, stream=stream)
+        res = {}
+        for mode in ("bool", "nearest"):
+            for name, lo in (("per_segment", None), ("packet", {"packet": 1})):
+                o = bvh.intersect(A, B, mode, launch=lo, stream=stream)
+                ms = timed(lambda: bvh.intersect(A, B, mode, launch=lo, out=o, stream=stream),
+                           steps, stream, torch)
+                res[f"{mode}_{name}"] = round(seg.n / (ms * 1e-3) / 1e6, 3)
+        out["coherent"] = {"workload": "heightfield 123x123 (29,768 tris) x 3163x3163 raster of "
+                                       "vertical segments (row by row)",
+                           "traverse_Msegs": res, "unit": UNIT}
+        del bvh, A, B
         # batched
         items = synth.workload_batched()
         tens = [(torch.from_numpy(m.V).to(dev), torch.from_numpy(m.T).to(dev),

@@ -121,6 +121,17 @@ typedef struct {
                             its records are built by one extra kernel on the
                             first 4-wide traversal after each build or
                             refit); 0 -> 2.  smem_nodes > 0 implies 2. */
+    int32_t packet;      /* 1: warp-cooperative traversal (f4, for coherent
+                            segments): each warp takes 32 consecutive
+                            segments in processing order and walks the tree
+                            once for all of them, descending into a child
+                            when any lane's segment enters it; results are
+                            the same.  Costs the union of the 32 paths, so
+                            use it with sort_bits or with inputs already
+                            ordered in space.  Requires node_width 0 / 2 and
+                            smem_nodes <= 0 (else RSI_ERR_ARG); block_size
+                            and stack_depth are ignored (128, 64).  0 -> one
+                            stack per segment. */
 } rsi_launch_opts;
 
 /* Per-segment outputs, all DEVICE pointers owned by the caller.  Which must be
@@ -365,7 +376,10 @@ typedef struct {
 /* Plan a batch of n items (host array, copied): allocates one concatenated
  * tree storage for all meshes and a work list of (item, segment chunk) tiles
  * ordered by estimated cost (N_r log N_t), largest first.  The item pointers
- * are stored: they must stay valid for the plan's lifetime.
+ * are stored: they must stay valid for the plan's lifetime.  From lo the
+ * batch uses block_size and stack_depth (the batched kernel traverses binary
+ * nodes with one stack per segment, in input order); the other fields are
+ * validated and otherwise ignored.
  * Errors: RSI_ERR_ARG, RSI_ERR_OOM, RSI_ERR_CUDA. */
 rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n,
                             const rsi_build_opts* bo, const rsi_launch_opts* lo,
@@ -410,6 +424,18 @@ rsi_status rsi_autotune(rsi_bvh h, const float* dV, const int32_t* dT,
                         const int32_t* leaf_sizes, int32_t n_ls, int32_t reps,
                         rsi_stream s, rsi_tune_entry* table, int32_t cap,
                         int32_t* n_written, rsi_launch_opts* best_lo, int32_t* best_leaf);
+
+/* --------------------------------------------------------- measurement --- */
+
+/* FP32 peak probe (not part of the paper's method): launches an FMA-only
+ * kernel that fills every SM of the current device (8 independent chains
+ * per thread, `iters` FMAs per chain), times it with CUDA events on s after
+ * one short warm-up launch, and writes the measured FP32 rate in TFLOP/s
+ * (2 flops per FMA) to *tflops (host).  It is the ceiling the benchmark
+ * compares the traversal's box-test and triangle-test arithmetic with.
+ * Synchronises s; allocates 4 bytes (cudaMallocAsync on s).  Errors:
+ * RSI_ERR_ARG (iters < 1, tflops NULL), RSI_ERR_CUDA. */
+rsi_status rsi_fp32_peak(int64_t iters, double* tflops, rsi_stream s);
 
 #ifdef __cplusplus
 }

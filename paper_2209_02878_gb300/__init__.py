@@ -20,7 +20,7 @@ from . import _abi
 from ._abi import MODES, RSIError
 
 __all__ = ["BVH", "Batch", "intersect", "intersect_backward", "nearest_hit", "RSIFunction",
-           "RSIError", "MODES", "load_library", "library_version"]
+           "RSIError", "MODES", "load_library", "library_version", "fp32_peak"]
 
 
 def load_library():
@@ -29,6 +29,15 @@ def load_library():
 
 def library_version() -> str:
     return _abi.load().rsi_version().decode()
+
+
+def fp32_peak(iters: int = 1 << 16, stream=None) -> float:
+    """Measured FP32 rate of the current device in TFLOP/s (rsi_fp32_peak:
+    an FMA-only kernel over every SM, event-timed).  Synchronises."""
+    v = C.c_double(0.0)
+    _abi.check(_abi.load().rsi_fp32_peak(int(iters), C.byref(v), _stream(stream)),
+               "rsi_fp32_peak")
+    return v.value
 
 
 def _vp(t):

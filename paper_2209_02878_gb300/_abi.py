@@ -42,7 +42,7 @@ class rsi_build_opts(C.Structure):
 
 class rsi_launch_opts(C.Structure):
     _fields_ = [("block_size", i32), ("stack_depth", i32), ("smem_nodes", i32), ("stats", i32),
-                ("sort_bits", i32), ("node_width", i32)]
+                ("sort_bits", i32), ("node_width", i32), ("packet", i32)]
 
 
 class rsi_output(C.Structure):
@@ -102,6 +102,7 @@ _PROTOS = {
     "rsi_autotune": (C.c_int, [vp, vp, vp, vp, vp, i64, C.c_int, P(rsi_output),
                                P(i32), i32, P(i32), i32, P(i32), i32, P(i32), i32, i32, vp,
                                P(rsi_tune_entry), i32, P(i32), P(rsi_launch_opts), P(i32)]),
+    "rsi_fp32_peak": (C.c_int, [i64, P(C.c_double), vp]),
 }
 
 # every entry point declared in include/rsi.h

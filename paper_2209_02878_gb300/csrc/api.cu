@@ -83,7 +83,7 @@ rsi_status check_build_opts(const rsi_build_opts* o, int32_t* leaf, int32_t* lev
 
 struct LaunchCfg {
     int block, stack, smem_nodes, sort_bits, width;
-    bool stats;
+    bool stats, packet;
 };
 
 rsi_status check_launch_opts(const rsi_launch_opts* lo, bool has_treelet, LaunchCfg* c) {
@@ -93,6 +93,7 @@ rsi_status check_launch_opts(const rsi_launch_opts* lo, bool has_treelet, Launch
     c->sort_bits = 0;
     c->width = 2;
     c->stats = false;
+    c->packet = false;
     int sm = 0;
     if (lo) {
         if (lo->block_size != 0) {
@@ -112,6 +113,9 @@ rsi_status check_launch_opts(const rsi_launch_opts* lo, bool has_treelet, Launch
         if (lo->node_width != 0 && lo->node_width != 2 && lo->node_width != 4) return RSI_ERR_ARG;
         if (lo->node_width != 0) c->width = lo->node_width;
         c->stats = lo->stats != 0;
+        if (lo->packet != 0 && lo->packet != 1) return RSI_ERR_ARG;
+        if (lo->packet == 1 && (lo->node_width == 4 || lo->smem_nodes > 0)) return RSI_ERR_ARG;
+        c->packet = lo->packet == 1;
     }
     if (has_treelet && sm > 0) c->smem_nodes = sm;
     if (c->smem_nodes > 0) c->width = 2;  // the treelet holds binary nodes
@@ -484,7 +488,10 @@ static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, in
         h->nodes4_valid = true;
     }
     if (c.stats) RSI_CK(cudaMemsetAsync(P.stats, 0, 6 * 8, (cudaStream_t)s));
-    RSI_CK(rsi::launch_trace(P, mode, c.stack, c.stats, c.block, c.width, (cudaStream_t)s));
+    if (c.packet)
+        RSI_CK(rsi::launch_trace_packet(P, mode, c.stats, (cudaStream_t)s));
+    else
+        RSI_CK(rsi::launch_trace(P, mode, c.stack, c.stats, c.block, c.width, (cudaStream_t)s));
     return RSI_OK;
 }
 

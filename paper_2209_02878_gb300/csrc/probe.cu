@@ -1,0 +1,74 @@
+// FP32 peak probe: the FP32 ceiling against which the traversal's box and
+// triangle arithmetic is compared (the traversal's own roofline is HBM
+// bandwidth nominally, issue rate in practice; this gives the third
+// ceiling).  Not part of the paper's method.
+//
+// Every thread runs kChains independent FMA chains for `iters` rounds, so
+// the FMA pipes never wait on a dependency; the grid fills every SM.  The
+// result is written only if it equals a value it cannot reach, which keeps
+// the chains live without memory traffic.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rsi.h"
+
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kProbeBlock = 256;
+
+__global__ void k_fma_probe(int64_t iters, float a, float b, float* sink) {
+    float x[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) x[k] = (float)(threadIdx.x + k);
+    for (int64_t r = 0; r < iters; ++r) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) x[k] = fmaf(x[k], a, b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += x[k];
+    if (s == -1.2345f) sink[0] = s;  // never true for the arguments used
+}
+
+}  // namespace
+
+extern "C" rsi_status rsi_fp32_peak(int64_t iters, double* tflops, rsi_stream s) {
+    if (iters < 1 || !tflops) return RSI_ERR_ARG;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_probe, kProbeBlock, 0) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return RSI_ERR_CUDA;
+    }
+    const int grid = sms * (per_sm > 0 ? per_sm : 1);
+    cudaStream_t cs = (cudaStream_t)s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float* sink = nullptr;
+    rsi_status st = RSI_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMallocAsync((void**)&sink, sizeof(float), cs) != cudaSuccess) {
+        st = RSI_ERR_CUDA;
+    } else {
+        // a,b keep the chains finite: x -> 0.5 x + 0.25 converges to 0.5
+        k_fma_probe<<<grid, kProbeBlock, 0, cs>>>(iters / 8 + 1, 0.5f, 0.25f, sink);  // warm-up
+        cudaEventRecord(e0, cs);
+        k_fma_probe<<<grid, kProbeBlock, 0, cs>>>(iters, 0.5f, 0.25f, sink);
+        cudaEventRecord(e1, cs);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) !=
+                                                           cudaSuccess || ms <= 0.f) {
+            st = RSI_ERR_CUDA;
+        } else {
+            const double flops = 2.0 * kChains * (double)iters * grid * kProbeBlock;
+            *tflops = flops / (ms * 1e-3) / 1e12;
+        }
+    }
+    if (sink) cudaFreeAsync(sink, cs);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess && st == RSI_OK) st = RSI_ERR_CUDA;
+    return st;
+}

@@ -32,6 +32,9 @@ struct TraceParams {
 cudaError_t launch_trace(const TraceParams& P, int mode, int stack, bool stats, int block,
                          int width, cudaStream_t s);
 
+// Enqueue one warp-cooperative (packet) traversal (packet.cu).
+cudaError_t launch_trace_packet(const TraceParams& P, int mode, bool stats, cudaStream_t s);
+
 // Persistent grid size for a kernel / block size / dynamic smem (cached).
 cudaError_t occupancy_grid(const void* fn, int block, int smem, int* grid);
 int sm_count(int dev);

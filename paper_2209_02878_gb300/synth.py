@@ -163,6 +163,18 @@ def segments_box(rng, n, lo_a, hi_a, lo_b, hi_b) -> Segments:
     return Segments(A, B)
 
 
+def segments_raster(g: int, z0=-1.0, z1=1.0) -> Segments:
+    """A g x g raster of vertical segments over [0,1]^2 (pixel centres, row
+    by row): the coherent input of an orthographic view, where neighbouring
+    segments take nearly the same path through the tree."""
+    xs = (np.arange(g, dtype=np.float64) + 0.5) / g
+    x, y = np.meshgrid(xs, xs, indexing="xy")
+    n = g * g
+    A = np.stack([x.ravel(), y.ravel(), np.full(n, z0)], axis=1).astype(np.float32)
+    B = np.stack([x.ravel(), y.ravel(), np.full(n, z1)], axis=1).astype(np.float32)
+    return Segments(A, B)
+
+
 def segments_random_direction(rng, n, V: np.ndarray, expand=0.10,
                               len_lo=0.01, len_hi=1.0, chunk=1 << 21) -> Segments:
     """Start uniform in the mesh bbox grown by `expand` of its extent per side,
@@ -223,6 +235,14 @@ def workload_diff(seed: int = 3, n_seg: int = 262_144, G: int = 257):
     B = np.concatenate([xy + dxy, np.ones((n_seg, 1))], axis=1).astype(np.float32)
     w = rng.normal(0.0, 1.0, size=(n_seg, 3)).astype(np.float32)
     return mesh, Segments(A, B), w
+
+
+def workload_raster(seed: int = 1, g: int = 3163, G: int = 123):
+    """The paper-scale heightfield (seed 1, 29,768 triangles) under a
+    3163 x 3163 raster of vertical segments (10,004,569, row by row)."""
+    rng = np.random.default_rng(seed)
+    mesh = heightfield(G, rng)
+    return mesh, segments_raster(g)
 
 
 ICO_LEVELS = (3, 4, 5, 6)  # 1,280 / 5,120 / 20,480 / 81,920 triangles
