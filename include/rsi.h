@@ -112,7 +112,7 @@ typedef struct {
                             order (measured faster for random segments).
                             Results do not depend on the order.  Needs a
                             workspace of 16 B per segment, allocated by the
-                            handle on first use (cudaMallocAsync on s) and
+                            handle on first use (device allocator, on s) and
                             kept for later calls of the same or smaller nR. */
     int32_t node_width;  /* traversal node arity: 2 (the binary tree, as in
                             the paper) or 4 (each visit tests the four
@@ -187,10 +187,31 @@ typedef struct {
 const char* rsi_version(void);
 const char* rsi_status_string(rsi_status s);
 
+/* ------------------------------------------------------ device memory --- */
+
+/* Caller-supplied device allocator (optional).  alloc returns `bytes` of
+ * device memory on `device`, usable in stream order on s, at least 256-byte
+ * aligned, or NULL when it cannot; free releases a pointer that alloc
+ * returned, in stream order on s (work already queued on s may still use
+ * it, as with cudaFreeAsync).  ctx is passed back unchanged. */
+typedef void* (*rsi_alloc_fn)(size_t bytes, int device, rsi_stream s, void* ctx);
+typedef void (*rsi_free_fn)(void* p, int device, rsi_stream s, void* ctx);
+
+/* Route every device allocation of the library (handle storage, workspaces,
+ * host-path staging, the adjoint's accumulator) through alloc / free, e.g.
+ * PyTorch's caching allocator, instead of cudaMallocAsync / cudaFreeAsync;
+ * both NULL restores the default.  Process-wide; a handle or batch keeps
+ * the pair that was set when it was created for all its memory, including
+ * the final free.  A NULL from alloc gives RSI_ERR_OOM, memory that is not
+ * 256-byte aligned is handed back and gives RSI_ERR_CUDA.  Not part of the
+ * paper.  Errors: RSI_ERR_ARG (exactly one of alloc, free NULL). */
+rsi_status rsi_set_allocator(rsi_alloc_fn alloc, rsi_free_fn free, void* ctx);
+
 /* ---------------------------------------------------------------- BVH --- */
 
 /* Allocate a handle for meshes of nV vertices and nT triangles (device memory
- * from cudaMallocAsync on stream s, ordered on s).  No tree is built yet.
+ * from the device allocator -- rsi_set_allocator, else cudaMallocAsync --
+ * on stream s, ordered on s).  No tree is built yet.
  * Sec. 2 / Sec. 3.1: the paper's internalNodes (N_t - 1) and leafNodes (N_t)
  * arrays; here one 64-byte node per internal node holding both child boxes,
  * plus a root slot, and the triangles re-stored in leaf order.
@@ -270,7 +291,7 @@ rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR
  * pointers; compaction (hout->hit_idx) is not supported.  The segments go
  * through in chunks of `chunk` (0 -> 2^21) on two internal streams with
  * double-buffered device staging (56 B per segment per buffer, allocated by
- * the handle on first use, cudaMallocAsync on s), so that the traversal of
+ * the handle on first use from the device allocator, on s), so that the traversal of
  * one chunk and the copy of the previous chunk's results back overlap.
  * When hA and hB both lie in page-locked memory the device can address
  * (cudaHostAlloc / cudaHostRegister, unified addressing), the traversal
@@ -294,7 +315,7 @@ rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64
  * mod 2.  A point whose test segment passes within the near-degenerate band
  * of an edge or vertex can get the wrong parity, as with any parity test.
  * Uses a workspace of 16 B per point held by the handle (allocated on first
- * use, cudaMallocAsync on s).  lo as for rsi_intersect (may be NULL).
+ * use from the device allocator, on s).  lo as for rsi_intersect (may be NULL).
  * Errors: RSI_ERR_ARG, RSI_ERR_NOT_BUILT, RSI_ERR_OOM, RSI_ERR_CUDA. */
 rsi_status rsi_points_inside(rsi_bvh h, const float* dP, int64_t nP, uint8_t* dInside,
                              const rsi_launch_opts* lo, rsi_stream s);
@@ -433,7 +454,7 @@ rsi_status rsi_autotune(rsi_bvh h, const float* dV, const int32_t* dT,
  * one short warm-up launch, and writes the measured FP32 rate in TFLOP/s
  * (2 flops per FMA) to *tflops (host).  It is the ceiling the benchmark
  * compares the traversal's box-test and triangle-test arithmetic with.
- * Synchronises s; allocates 4 bytes (cudaMallocAsync on s).  Errors:
+ * Synchronises s; allocates 4 bytes (device allocator, on s).  Errors:
  * RSI_ERR_ARG (iters < 1, tflops NULL), RSI_ERR_CUDA. */
 rsi_status rsi_fp32_peak(int64_t iters, double* tflops, rsi_stream s);
 

@@ -20,7 +20,8 @@ from . import _abi
 from ._abi import MODES, RSIError
 
 __all__ = ["BVH", "Batch", "intersect", "intersect_backward", "nearest_hit", "RSIFunction",
-           "RSIError", "MODES", "load_library", "library_version", "fp32_peak"]
+           "RSIError", "MODES", "load_library", "library_version", "fp32_peak",
+           "set_allocator", "use_torch_allocator"]
 
 
 def load_library():
@@ -38,6 +39,57 @@ def fp32_peak(iters: int = 1 << 16, stream=None) -> float:
     _abi.check(_abi.load().rsi_fp32_peak(int(iters), C.byref(v), _stream(stream)),
                "rsi_fp32_peak")
     return v.value
+
+
+_keep = []  # every ctypes callback pair ever set (handles may still free through one)
+
+
+def set_allocator(alloc=None, free=None):
+    """Route the library's device allocations through Python callables
+    (rsi_set_allocator): alloc(nbytes, device, stream) -> int pointer (0 when
+    it cannot), free(ptr, device, stream).  Streams are raw cudaStream_t
+    values (0 = the legacy default stream).  Both None restores
+    cudaMallocAsync / cudaFreeAsync.  Handles keep the allocator that was set
+    when they were created."""
+    lib = _abi.load()
+    if alloc is None and free is None:
+        _abi.check(lib.rsi_set_allocator(None, None, None), "rsi_set_allocator")
+        return
+    if alloc is None or free is None:
+        raise ValueError("set both alloc and free, or neither")
+
+    def _a(nbytes, device, stream, ctx):
+        return int(alloc(int(nbytes), int(device), int(stream or 0)) or 0) or None
+
+    def _f(p, device, stream, ctx):
+        free(int(p), int(device), int(stream or 0))
+
+    ca, cf = _abi.ALLOC_FN(_a), _abi.FREE_FN(_f)
+    _abi.check(lib.rsi_set_allocator(C.cast(ca, C.c_void_p), C.cast(cf, C.c_void_p), None),
+               "rsi_set_allocator")
+    # handles created under these callbacks free through them later: keep
+    # every pair alive for the life of the process
+    _keep.append((ca, cf))
+
+
+def use_torch_allocator(enable: bool = True):
+    """Take the library's device memory from PyTorch's caching allocator
+    (it then shows in torch.cuda.memory_allocated and can be reused by
+    torch), or go back to cudaMallocAsync."""
+    if not enable:
+        set_allocator(None, None)
+        return
+
+    def alloc(nbytes, device, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(nbytes, device=device, stream=stream)
+        except RuntimeError:
+            return 0
+
+    def free(p, device, stream):
+        torch.cuda.caching_allocator_delete(p)
+
+    set_allocator(alloc, free)
 
 
 def _vp(t):

@@ -40,6 +40,11 @@ class rsi_build_opts(C.Structure):
     _fields_ = [("leaf_size", i32), ("top_levels", i32)]
 
 
+# rsi_alloc_fn / rsi_free_fn (pass as c_void_p after ctypes.cast)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_int, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p)
+
+
 class rsi_launch_opts(C.Structure):
     _fields_ = [("block_size", i32), ("stack_depth", i32), ("smem_nodes", i32), ("stats", i32),
                 ("sort_bits", i32), ("node_width", i32), ("packet", i32)]
@@ -103,6 +108,7 @@ _PROTOS = {
                                P(i32), i32, P(i32), i32, P(i32), i32, P(i32), i32, i32, vp,
                                P(rsi_tune_entry), i32, P(i32), P(rsi_launch_opts), P(i32)]),
     "rsi_fp32_peak": (C.c_int, [i64, P(C.c_double), vp]),
+    "rsi_set_allocator": (C.c_int, [vp, vp, vp]),
 }
 
 # every entry point declared in include/rsi.h

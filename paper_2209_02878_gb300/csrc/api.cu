@@ -179,6 +179,7 @@ struct rsi_bvh_s {
     char* in_mem = nullptr;
     int64_t in_cap = 0;
     cudaStream_t in_stream = nullptr;
+    rsi::AllocHooks hooks{};  // device allocator of all this handle's memory
 };
 
 namespace {
@@ -186,14 +187,14 @@ namespace {
 rsi_status ensure_seg_ws(rsi_bvh h, int64_t n, cudaStream_t s) {
     if (h->seg_mem && h->seg_ws.cap >= n) return RSI_OK;
     if (h->seg_mem) {
-        cudaFreeAsync(h->seg_mem, s);
+        rsi::dev_free(h->hooks, h->seg_mem, s);
         h->seg_mem = nullptr;
     }
     const int64_t ntiles = (n + rsi::kSortTileMin - 1) / rsi::kSortTileMin;
     const size_t b1 = align256(4 * (size_t)n);
     const size_t bh = align256(4 * (size_t)rsi::kSortBins * (size_t)(ntiles > 0 ? ntiles : 1));
     const size_t bytes = 4 * b1 + bh + align256(4 * rsi::kSortBins);
-    cudaError_t e = cudaMallocAsync((void**)&h->seg_mem, bytes, s);
+    cudaError_t e = rsi::dev_alloc(h->hooks, (void**)&h->seg_mem, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         h->seg_mem = nullptr;
@@ -240,8 +241,11 @@ rsi_status rsi_bvh_create(int64_t nV, int64_t nT, const rsi_build_opts* opt, rsi
     int32_t leaf, levels;
     rsi_status st = check_build_opts(opt, &leaf, &levels);
     if (st != RSI_OK) return st;
+    int device = 0;
+    RSI_CK(cudaGetDevice(&device));
     rsi_bvh h = new rsi_bvh_s();
-    RSI_CK(cudaGetDevice(&h->device));
+    h->hooks = rsi::current_hooks();
+    h->device = device;
     h->nV = nV;
     h->nT = nT;
     h->leaf = leaf;
@@ -251,7 +255,7 @@ rsi_status rsi_bvh_create(int64_t nV, int64_t nT, const rsi_build_opts* opt, rsi
     memset(&tb, 0, sizeof(tb));
     size_t bytes = carve(tb, nT, 1, nblk, nullptr) + 256;
     cudaStream_t cs = (cudaStream_t)s;
-    cudaError_t e = cudaMallocAsync((void**)&h->mem, bytes, cs);
+    cudaError_t e = rsi::dev_alloc(h->hooks, (void**)&h->mem, bytes, cs);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -269,7 +273,7 @@ rsi_status rsi_bvh_create(int64_t nV, int64_t nT, const rsi_build_opts* opt, rsi
     if (e == cudaSuccess) e = cudaMemsetAsync(tb.treelet_n, 0, 4, cs);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFreeAsync(h->mem, cs);
+        rsi::dev_free(h->hooks, h->mem, cs);
         delete h;
         return RSI_ERR_CUDA;
     }
@@ -358,15 +362,15 @@ rsi_status rsi_bvh_destroy(rsi_bvh h) {
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != h->device) cudaSetDevice(h->device);
-    if (h->seg_mem) cudaFreeAsync(h->seg_mem, h->seg_stream);
-    if (h->pipe_mem) cudaFreeAsync(h->pipe_mem, h->pipe_stream);
-    if (h->in_mem) cudaFreeAsync(h->in_mem, h->in_stream);
+    if (h->seg_mem) rsi::dev_free(h->hooks, h->seg_mem, h->seg_stream);
+    if (h->pipe_mem) rsi::dev_free(h->hooks, h->pipe_mem, h->pipe_stream);
+    if (h->in_mem) rsi::dev_free(h->hooks, h->in_mem, h->in_stream);
     for (int q = 0; q < 2; ++q) {
         if (h->pst[q]) cudaStreamDestroy(h->pst[q]);
         if (h->pev_done[q]) cudaEventDestroy(h->pev_done[q]);
     }
     if (h->pev_start) cudaEventDestroy(h->pev_start);
-    cudaError_t e = cudaFreeAsync(h->mem, h->stream);
+    cudaError_t e = rsi::dev_free(h->hooks, h->mem, h->stream);
     if (cur != h->device) cudaSetDevice(cur);
     delete h;
     if (e != cudaSuccess) {
@@ -592,11 +596,11 @@ rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64
     const size_t per_buf = 2 * in_b + out_b;
     if (h->pipe_bytes < 2 * per_buf) {
         if (h->pipe_mem) {
-            RSI_CK(cudaFreeAsync(h->pipe_mem, h->pipe_stream));
+            RSI_CK(rsi::dev_free(h->hooks, h->pipe_mem, h->pipe_stream));
             h->pipe_mem = nullptr;
             h->pipe_bytes = 0;
         }
-        cudaError_t e = cudaMallocAsync((void**)&h->pipe_mem, 2 * per_buf, cs);
+        cudaError_t e = rsi::dev_alloc(h->hooks, (void**)&h->pipe_mem, 2 * per_buf, cs);
         if (e != cudaSuccess) {
             cudaGetLastError();
             h->pipe_mem = nullptr;
@@ -674,10 +678,10 @@ rsi_status rsi_points_inside(rsi_bvh h, const float* dP, int64_t nP, uint8_t* dI
     }
     if (h->in_cap < nP) {
         if (h->in_mem) {
-            RSI_CK(cudaFreeAsync(h->in_mem, h->in_stream));
+            RSI_CK(rsi::dev_free(h->hooks, h->in_mem, h->in_stream));
             h->in_mem = nullptr;
         }
-        cudaError_t e = cudaMallocAsync((void**)&h->in_mem, (size_t)(16 * nP + 512), cs);
+        cudaError_t e = rsi::dev_alloc(h->hooks, (void**)&h->in_mem, (size_t)(16 * nP + 512), cs);
         if (e != cudaSuccess) {
             cudaGetLastError();
             h->in_mem = nullptr;
@@ -732,6 +736,7 @@ struct rsi_batch_s {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t g_full = nullptr, g_trav = nullptr;
     cudaStream_t stream = nullptr;
+    rsi::AllocHooks hooks{};  // device allocator of all this batch's memory
 };
 
 extern "C" {
@@ -800,8 +805,11 @@ rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_bu
             tiles.push_back(t);
         }
     }
+    int device = 0;
+    RSI_CK(cudaGetDevice(&device));
     rsi_batch b = new rsi_batch_s();
-    RSI_CK(cudaGetDevice(&b->device));
+    b->hooks = rsi::current_hooks();
+    b->device = device;
     b->items.assign(items, items + n);
     b->cfg = cfg;
     b->leaf = leaf;
@@ -815,7 +823,7 @@ rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_bu
     const size_t tile_bytes = align256(sizeof(rsi::BatchTile) * (tiles.size() + 1));
     const size_t bytes = tree_bytes + tab_bytes + blk_bytes + item_bytes + tile_bytes + 256;
     cudaStream_t cs = (cudaStream_t)s;
-    cudaError_t e = cudaMallocAsync((void**)&b->mem, bytes, cs);
+    cudaError_t e = rsi::dev_alloc(b->hooks, (void**)&b->mem, bytes, cs);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete b;
@@ -847,7 +855,7 @@ rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_bu
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFreeAsync(b->mem, cs);
+        rsi::dev_free(b->hooks, b->mem, cs);
         delete b;
         return RSI_ERR_CUDA;
     }
@@ -923,7 +931,7 @@ rsi_status rsi_batch_destroy(rsi_batch b) {
     if (b->g_full) cudaGraphExecDestroy(b->g_full);
     if (b->g_trav) cudaGraphExecDestroy(b->g_trav);
     cudaStreamSynchronize(b->stream);
-    cudaError_t e = cudaFreeAsync(b->mem, b->stream);
+    cudaError_t e = rsi::dev_free(b->hooks, b->mem, b->stream);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     if (e != cudaSuccess) {

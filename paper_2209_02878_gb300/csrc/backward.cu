@@ -104,11 +104,15 @@ cudaError_t launch_backward(const float* V, int64_t nV, const int32_t* T, int64_
     double* acc = nullptr;
     const size_t bytes = sizeof(double) * 3 * (size_t)(nV > 0 ? nV : 1);
     cudaError_t e = cudaSuccess;
+    const AllocHooks hooks = current_hooks();
     if (gV) {
-        e = cudaMallocAsync((void**)&acc, bytes, s);
+        e = dev_alloc(hooks, (void**)&acc, bytes, s);
         if (e != cudaSuccess) return e;
         e = cudaMemsetAsync(acc, 0, bytes, s);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) {
+            dev_free(hooks, acc, s);
+            return e;
+        }
     }
     k_backward<<<(unsigned)((nR + block - 1) / block), block, 0, s>>>(V, nV, T, nT, A, B, nR, tri,
                                                                      gP, gtuv, acc, gA, gB);
@@ -118,7 +122,7 @@ cudaError_t launch_backward(const float* V, int64_t nV, const int32_t* T, int64_
         e = cudaGetLastError();
     }
     if (acc) {
-        const cudaError_t f = cudaFreeAsync(acc, s);
+        const cudaError_t f = dev_free(hooks, acc, s);
         if (e == cudaSuccess) e = f;
     }
     return e;

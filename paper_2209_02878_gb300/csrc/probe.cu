@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include "rsi.h"
+#include "rsi_trace.h"
 
 namespace {
 
@@ -48,8 +49,9 @@ extern "C" rsi_status rsi_fp32_peak(int64_t iters, double* tflops, rsi_stream s)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float* sink = nullptr;
     rsi_status st = RSI_OK;
+    const rsi::AllocHooks hooks = rsi::current_hooks();
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
-        cudaMallocAsync((void**)&sink, sizeof(float), cs) != cudaSuccess) {
+        rsi::dev_alloc(hooks, (void**)&sink, sizeof(float), cs) != cudaSuccess) {
         st = RSI_ERR_CUDA;
     } else {
         // a,b keep the chains finite: x -> 0.5 x + 0.25 converges to 0.5
@@ -66,7 +68,7 @@ extern "C" rsi_status rsi_fp32_peak(int64_t iters, double* tflops, rsi_stream s)
             *tflops = flops / (ms * 1e-3) / 1e12;
         }
     }
-    if (sink) cudaFreeAsync(sink, cs);
+    if (sink) rsi::dev_free(hooks, sink, cs);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (cudaGetLastError() != cudaSuccess && st == RSI_OK) st = RSI_ERR_CUDA;

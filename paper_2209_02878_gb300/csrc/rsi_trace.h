@@ -8,6 +8,17 @@
 
 namespace rsi {
 
+// Device allocator in effect (rsi_set_allocator); null hooks mean
+// cudaMallocAsync / cudaFreeAsync.  alloc.cu.
+struct AllocHooks {
+    rsi_alloc_fn alloc;
+    rsi_free_fn free;
+    void* ctx;
+};
+AllocHooks current_hooks();
+cudaError_t dev_alloc(const AllocHooks& h, void** p, size_t bytes, cudaStream_t s);
+cudaError_t dev_free(const AllocHooks& h, void* p, cudaStream_t s);
+
 struct TraceParams {
     const float* A;
     const float* B;

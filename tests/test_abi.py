@@ -101,3 +101,6 @@ def test_argument_validation_without_gpu(lib):
     v = ctypes.c_double(0.0)
     assert L.rsi_fp32_peak(0, ctypes.byref(v), None) == _abi.RSI_ERR_ARG
     assert L.rsi_fp32_peak(10, None, None) == _abi.RSI_ERR_ARG
+    cb = _abi.ALLOC_FN(lambda n, d, s, c: None)
+    assert L.rsi_set_allocator(ctypes.cast(cb, ctypes.c_void_p), None, None) == _abi.RSI_ERR_ARG
+    assert L.rsi_set_allocator(None, None, None) == _abi.RSI_OK
