@@ -41,6 +41,7 @@ __global__ void __maxnreg__(128) k_batch(BatchParams P) {
         C.snodes = nullptr;
         C.S = 0;
         C.max_visits = P.max_visits;
+        C.fetch = kFetchChunk;  // unused: each tile is one warp's whole pool
         C.order = nullptr;
         C.status = P.status;
         C.out = it.out;

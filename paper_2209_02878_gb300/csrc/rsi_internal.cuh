@@ -262,19 +262,34 @@ __device__ __forceinline__ void slab2(const Seg& s, const ulonglong2& q0, const 
     h1 = tn1 <= tf.y;
 }
 
-// FP32 Moller-Trumbore with a static error filter.
+// FP32 Moller-Trumbore with a two-stage error filter.
 //
-// With u = 2^-24 and exact float inputs, each computed triple product
-// (det = e1.(d x e2), nU = s0.(d x e2), nV = d.(s0 x e1), nT = e2.(s0 x e1))
-// differs from its exact value by at most 6 gamma_8 m_a m_b m_c (< 48u M),
-// where m_x = max_i |x_i| of the three factors (FMA contraction only removes
-// roundings).  The two derived sums det - nU - nV and det - nT add <= 12u of
-// their magnitude.  A decision is certified when the value clears
-// K M + eta with K = 2^-17 (> 60u plus the FP64 definition's own error and
-// the rounding of M itself); eta covers underflow when every m lies in
-// [2^-30, 2^30] (else the FP64 path decides).  Certified decisions equal
-// those of the FP64 definition; the rest return 2 and are decided in FP64.
-// Returns 0 miss, 1 hit, 2 undecided.
+// With u = 2^-24 and exact float inputs, every elementary term of a computed
+// triple product (det = e1.(d x e2), nU = s0.(d x e2), nV = d.(s0 x e1),
+// nT = e2.(s0 x e1)), e.g. s0x d_y e2z, carries at most 8 roundings (the
+// three input differences, the product, the cross-product difference, the
+// dot product's product and two sums; FMA contraction only removes
+// roundings), so |computed - exact| <= gamma_8 M with the componentwise sum
+// M = sum_i |x_i| (|y_j| |z_k| + |y_k| |z_j|) <= 6 m_x m_y m_z (m = max_i).
+//  - Stage 1 (cheap): B = K m_x m_y m_z + eta, K = 2^-17 (> 6 gamma_8 plus
+//    the FP64 definition's own error and the rounding of the bound).
+//  - Stage 2, only when stage 1 cannot decide: B = g M~ + eta with M~
+//    evaluated from the computed factors (3 + 5 more roundings) and
+//    g = 11u (> gamma_8 (1 + gamma_8) plus the FP64 definition's gamma_8 of
+//    2^-53).  For long segments over small triangles it is far tighter:
+//    |s0| multiplies only the components of d x e2 it meets.
+// The derived sums w = det - nU - nV and r = det - nT add 12u of their
+// operands' magnitudes (stage 1, folded into K) or their two / one
+// roundings (stage 2, 2.01u / 1.01u).  eta = 2^-100 covers absolute errors
+// from underflow while every factor's max lies in [2^-30, 2^30] (else the
+// FP64 path decides, as it does for a zero or out-of-range value).  A value
+// whose computed magnitude clears its bound has the sign of the exact value,
+// and so of the FP64 definition's value: certified decisions equal the
+// definition's; the rest return 2 and are decided in FP64.  Returns 0 miss,
+// 1 hit, 2 undecided; with `want` also (t, u, v) and a bound err on their
+// errors against the exact values, (B_x + |x~| B_det) / (|det~| - B_det)
+// plus the two roundings of x~ = n_x * fl(1 / |det~|), from the bounds of
+// the stage that decided.
 __device__ __forceinline__ int mt32(const Seg& s, const float4& A, const float4& B,
                                     const float4& C, bool want, float& t, float& u, float& v,
                                     float& err) {
@@ -286,6 +301,9 @@ __device__ __forceinline__ int mt32(const Seg& s, const float4& A, const float4&
     if (m1 == 0.f || m2 == 0.f) return 0;
     const float sx = s.ax - A.x, sy = s.ay - A.y, sz = s.az - A.z;
     const float ms = maxabs3(sx, sy, sz);
+    const float mhi = fmaxf(fmaxf(m1, m2), ms);
+    const float mlo = fminf(fminf(m1, m2), ms == 0.f ? 1.f : ms);
+    if (s.fp64only || mhi > kRangeHi || mlo < kRangeLo) return 2;
     const float px = s.dy * e2z - s.dz * e2y;
     const float py = s.dz * e2x - s.dx * e2z;
     const float pz = s.dx * e2y - s.dy * e2x;
@@ -296,38 +314,58 @@ __device__ __forceinline__ int mt32(const Seg& s, const float4& A, const float4&
     float nu = sx * px + sy * py + sz * pz;
     float nv = s.dx * qx + s.dy * qy + s.dz * qz;
     float nt = e2x * qx + e2y * qy + e2z * qz;
-    const float mhi = fmaxf(fmaxf(m1, m2), ms);
-    const float mlo = fminf(fminf(m1, m2), ms == 0.f ? 1.f : ms);
-    if (s.fp64only || mhi > kRangeHi || mlo < kRangeLo) return 2;
-    const float Pde = s.md * m2, Pse = ms * m1;
-    const float Mdet = m1 * Pde, MU = ms * Pde, MV = s.md * Pse, MT = m2 * Pse;
-    const float Bdet = fmaf(kFilterK, Mdet, kFilterEta);
     const float adet = fabsf(det);
-    if (!(adet > Bdet)) return 2;
-    if (det < 0.f) {
+    if (det < 0.f) {  // used only once a stage has certified the sign of det
         nu = -nu;
         nv = -nv;
         nt = -nt;
     }
     const float w = (adet - nu) - nv;
     const float r = adet - nt;
-    const float BU = fmaf(kFilterK, MU, kFilterEta);
-    const float BV = fmaf(kFilterK, MV, kFilterEta);
-    const float BT = fmaf(kFilterK, MT, kFilterEta);
-    const float Bw = fmaf(kFilterK, Mdet + MU + MV, kFilterEta);
-    const float Br = fmaf(kFilterK, Mdet + MT, kFilterEta);
-    if (nu < -BU || nv < -BV || nt < -BT || w < -Bw || r < -Br) return 0;
-    if (!(nu > BU && nv > BV && nt > BT && w > Bw && r > Br)) return 2;
+    float Bdet, BU, BV, BT;
+    int res = 2;
+    {  // stage 1: max-norm bounds
+        const float Pde = s.md * m2, Pse = ms * m1;
+        const float Mdet = m1 * Pde, MU = ms * Pde, MV = s.md * Pse, MT = m2 * Pse;
+        Bdet = fmaf(kFilterK, Mdet, kFilterEta);
+        BU = fmaf(kFilterK, MU, kFilterEta);
+        BV = fmaf(kFilterK, MV, kFilterEta);
+        BT = fmaf(kFilterK, MT, kFilterEta);
+        const float Bw = fmaf(kFilterK, Mdet + MU + MV, kFilterEta);
+        const float Br = fmaf(kFilterK, Mdet + MT, kFilterEta);
+        if (adet > Bdet) {
+            if (nu < -BU || nv < -BV || nt < -BT || w < -Bw || r < -Br) return 0;
+            if (nu > BU && nv > BV && nt > BT && w > Bw && r > Br) res = 1;
+        }
+    }
+    if (res == 2) {  // stage 2: componentwise bounds
+        const float g = 11.f * 0x1p-24f;
+        const float Px = fabsf(s.dy) * fabsf(e2z) + fabsf(s.dz) * fabsf(e2y);
+        const float Py = fabsf(s.dz) * fabsf(e2x) + fabsf(s.dx) * fabsf(e2z);
+        const float Pz = fabsf(s.dx) * fabsf(e2y) + fabsf(s.dy) * fabsf(e2x);
+        const float Qx = fabsf(sy) * fabsf(e1z) + fabsf(sz) * fabsf(e1y);
+        const float Qy = fabsf(sz) * fabsf(e1x) + fabsf(sx) * fabsf(e1z);
+        const float Qz = fabsf(sx) * fabsf(e1y) + fabsf(sy) * fabsf(e1x);
+        Bdet = fmaf(g, fabsf(e1x) * Px + fabsf(e1y) * Py + fabsf(e1z) * Pz, kFilterEta);
+        if (!(adet > Bdet)) return 2;
+        BU = fmaf(g, fabsf(sx) * Px + fabsf(sy) * Py + fabsf(sz) * Pz, kFilterEta);
+        BV = fmaf(g, fabsf(s.dx) * Qx + fabsf(s.dy) * Qy + fabsf(s.dz) * Qz, kFilterEta);
+        BT = fmaf(g, fabsf(e2x) * Qx + fabsf(e2y) * Qy + fabsf(e2z) * Qz, kFilterEta);
+        const float Bw = fmaf(2.01f * 0x1p-24f, adet + fabsf(nu) + fabsf(nv), Bdet + BU + BV);
+        const float Br = fmaf(1.01f * 0x1p-24f, adet + fabsf(nt), Bdet + BT);
+        if (nu < -BU || nv < -BV || nt < -BT || w < -Bw || r < -Br) return 0;
+        if (!(nu > BU && nv > BV && nt > BT && w > Bw && r > Br)) return 2;
+    }
     if (want) {
         const float inv = __frcp_rn(adet);
         t = nt * inv;
         u = nu * inv;
         v = nv * inv;
-        // |x_computed - x| <= (B_x + |x| B_det) / |det| + 4u |x|
-        const float eT = fmaf(t, Bdet, BT) * inv;
-        const float eU = fmaf(u, Bdet, BU) * inv;
-        const float eV = fmaf(v, Bdet, BV) * inv;
-        err = fmaxf(fmaxf(eT, eU), eV) * 1.0001f + 0x1p-21f;
+        const float den = __frcp_rn(adet - Bdet);
+        const float eT = fmaf(t, Bdet, BT) * den;
+        const float eU = fmaf(u, Bdet, BU) * den;
+        const float eV = fmaf(v, Bdet, BV) * den;
+        err = fmaxf(fmaxf(eT, eU), eV) * 1.001f + 0x1p-22f;
     }
     return 1;
 }

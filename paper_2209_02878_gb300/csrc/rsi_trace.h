@@ -34,6 +34,7 @@ struct TraceParams {
     unsigned long long* work;   // zeroed before each launch
     unsigned long long* stats;  // 6 counters (STATS launches)
     int max_visits;             // node fetches per segment before giving up
+    int fetch;                  // segments per warp fetch (set by launch_trace)
     const int32_t* order;       // optional coherent processing order (nullptr = identity)
     int32_t* status;
     TravOut out;

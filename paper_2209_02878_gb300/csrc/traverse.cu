@@ -1,7 +1,7 @@
 // Single-mesh traversal launch (arXiv 2209.02878, Sec. 3.3
 // bvhIntersectionKernel): a persistent grid sized from the occupancy query
 // (the paper's N_grid lesson, Sec. 3.3: fill the machine), each warp pulling
-// kFetchChunk segments at a time from an atomic counter, optionally the top
+// a chunk of segments at a time from an atomic counter, optionally the top
 // treelet staged once per block in shared memory.
 #include <cuda_runtime.h>
 
@@ -42,6 +42,7 @@ __global__ void __maxnreg__(TraceRegs<MODE>::value) k_trace(TraceParams P) {
     C.snodes = snodes;
     C.S = S;
     C.max_visits = P.max_visits;
+    C.fetch = P.fetch;
     C.order = P.order;
     C.status = P.status;
     C.out = P.out;
@@ -141,7 +142,14 @@ cudaError_t launch_trace(const TraceParams& P, int mode, int stack, bool stats, 
     int grid = 0;
     cudaError_t e = occupancy_grid((const void*)fn, block, smem, &grid);
     if (e != cudaSuccess) return e;
-    const int64_t warps_needed = (P.nR + kFetchChunk - 1) / kFetchChunk;
+    // chunk size: about four chunks per resident warp, a multiple of 32 in
+    // [kFetchMin, kFetchChunk]
+    const int64_t warps = (int64_t)grid * (block / 32);
+    int64_t f = P.nR / (4 * warps);
+    f = f < kFetchMin ? kFetchMin : f > kFetchChunk ? kFetchChunk : f / 32 * 32;
+    TraceParams Q = P;
+    Q.fetch = (int)f;
+    const int64_t warps_needed = (P.nR + f - 1) / f;
     const int64_t blocks_needed = (warps_needed + block / 32 - 1) / (block / 32);
     if (blocks_needed < grid) grid = (int)blocks_needed;
     if (grid < 1) grid = 1;
@@ -151,7 +159,7 @@ cudaError_t launch_trace(const TraceParams& P, int mode, int stack, bool stats, 
         e = cudaMemsetAsync(P.out.n_hits, 0, sizeof(int64_t), s);
         if (e != cudaSuccess) return e;
     }
-    fn<<<grid, block, smem, s>>>(P);
+    fn<<<grid, block, smem, s>>>(Q);
     return cudaGetLastError();
 }
 

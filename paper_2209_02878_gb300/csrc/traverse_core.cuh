@@ -161,6 +161,7 @@ struct TraceCtx {
     const float4* snodes;  // shared-memory copy of treelet[0..S)
     int S;
     int max_visits;
+    int fetch;             // segments a warp takes from the counter at once
     const int32_t* order;  // optional processing order of the segments
     int32_t* status;
     TravOut out;
@@ -463,7 +464,11 @@ __device__ __forceinline__ void compact(const TravOut& o, bool has, int64_t i, c
     }
 }
 
-constexpr int kFetchChunk = 128;  // segments a warp takes from the global counter at once
+// Segments a warp takes from the global counter at once: kFetchChunk for
+// large launches (one atomic per 4 segments per lane), down to kFetchMin so
+// that a launch of few segments still gives every resident warp work.
+constexpr int kFetchChunk = 128;
+constexpr int kFetchMin = 32;
 constexpr int kRefillMin = 8;     // idle lanes that trigger a refill of a busy warp
 
 // Persistent per-warp traversal loop over segments [lo, hi).  Every lane
@@ -473,7 +478,7 @@ constexpr int kRefillMin = 8;     // idle lanes that trigger a refill of a busy 
 // lane and the divergent segment setup runs for several lanes at once.  A
 // finished lane keeps its result until that refill and writes it then,
 // together with the other finished lanes.  The pool is refilled with
-// kFetchChunk segments from *counter (one atomic per chunk), or, with
+// C.fetch segments from *counter (one atomic per chunk), or, with
 // counter == nullptr, holds the whole range [lo, hi) from the start.  When
 // `order` is given, pool position k processes segment order[k] (a coherent
 // ordering of the segments); outputs still go to the segment's own index.
@@ -517,14 +522,14 @@ __device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long
             if (pool >= pool_end) {
                 if (!more) break;
                 unsigned long long b = 0ull;
-                if (lane == 0) b = atomicAdd(counter, (unsigned long long)kFetchChunk);
+                if (lane == 0) b = atomicAdd(counter, (unsigned long long)C.fetch);
                 b = __shfl_sync(FULL, b, 0);
                 if (b >= (unsigned long long)hi) {
                     more = false;
                     break;
                 }
                 pool = (int64_t)b;
-                pool_end = pool + kFetchChunk < hi ? pool + kFetchChunk : hi;
+                pool_end = pool + C.fetch < hi ? pool + C.fetch : hi;
             }
             const int64_t left = pool_end - pool;
             const int avail = left < (int64_t)__popc(idle) ? (int)left : __popc(idle);
