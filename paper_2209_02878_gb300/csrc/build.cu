@@ -350,48 +350,53 @@ __global__ void k_climb(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ k
         return;
     }
     int node = tb.parent[N + g];
+    // The climbing thread carries its own subtree (child code, box, first
+    // leaf, size), so after the atomic only the sibling's box and range are
+    // loaded; the node's child pair and parent (written by k_karras) are
+    // loaded before the atomic so that their latency overlaps it.
+    int me = -g - 1;
+    float4 mlo = lo, mhi = hi;
+    int mfirst = g, msize = 1;
     // a radix tree over 62-bit keys is at most 63 levels deep
     for (int climb = 0;; ++climb) {
         if (climb > 70 || node < off || node >= off + n - 1) {
             latch(tb.status, RSI_ERR_INTERNAL);
             return;
         }
+        const int2 cc = *(const int2*)(tb.child + 2 * (int64_t)node);
+        const int par = tb.parent[node];
         // acquire-release: the first arrival publishes its child's box and
         // node record, the second arrival sees them
         if (atomic_add_acq_rel(&tb.flag[node], 1) == 0) return;  // the sibling finishes it
-        const int ch[2] = {tb.child[2 * node], tb.child[2 * node + 1]};
-        float4 cl[2], chh[2];
-        int ref[2], cnt[2];
-        for (int k = 0; k < 2; ++k) {
-            const int x = ch[k];
-            int size, first;
-            if (x < 0) {
-                const int leaf = -x - 1;
-                cl[k] = __ldcg(tb.lbox + 2 * (int64_t)leaf);
-                chh[k] = __ldcg(tb.lbox + 2 * (int64_t)leaf + 1);
-                size = 1;
-                first = leaf;
-            } else {
-                cl[k] = __ldcg(tb.nbox + 2 * (int64_t)x);
-                chh[k] = __ldcg(tb.nbox + 2 * (int64_t)x + 1);
-                first = tb.range[2 * x];
-                size = tb.range[2 * x + 1] - first + 1;
-            }
-            if (size <= L) {
-                ref[k] = first;
-                cnt[k] = size;
-            } else {
-                ref[k] = x;
-                cnt[k] = 0;
-            }
+        const bool mine0 = cc.x == me;
+        const int x = mine0 ? cc.y : cc.x;  // the sibling
+        float4 slo, shi;
+        int sfirst, ssize;
+        if (x < 0) {
+            const int leaf = -x - 1;
+            slo = __ldcg(tb.lbox + 2 * (int64_t)leaf);
+            shi = __ldcg(tb.lbox + 2 * (int64_t)leaf + 1);
+            sfirst = leaf;
+            ssize = 1;
+        } else {
+            slo = __ldcg(tb.nbox + 2 * (int64_t)x);
+            shi = __ldcg(tb.nbox + 2 * (int64_t)x + 1);
+            const int2 rg = *(const int2*)(tb.range + 2 * (int64_t)x);
+            sfirst = rg.x;
+            ssize = rg.y - rg.x + 1;
         }
-        const float4 ulo = make_float4(fminf(cl[0].x, cl[1].x), fminf(cl[0].y, cl[1].y),
-                                       fminf(cl[0].z, cl[1].z), 0.f);
-        const float4 uhi = make_float4(fmaxf(chh[0].x, chh[1].x), fmaxf(chh[0].y, chh[1].y),
-                                       fmaxf(chh[0].z, chh[1].z), 0.f);
+        // children in the node's order: 0 = cc.x, 1 = cc.y
+        const float4 l0 = mine0 ? mlo : slo, h0 = mine0 ? mhi : shi;
+        const float4 l1 = mine0 ? slo : mlo, h1 = mine0 ? shi : mhi;
+        const int f0 = mine0 ? mfirst : sfirst, z0 = mine0 ? msize : ssize;
+        const int f1 = mine0 ? sfirst : mfirst, z1 = mine0 ? ssize : msize;
+        const int ref0 = z0 <= L ? f0 : cc.x, cnt0 = z0 <= L ? z0 : 0;
+        const int ref1 = z1 <= L ? f1 : cc.y, cnt1 = z1 <= L ? z1 : 0;
+        const float4 ulo = make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.f);
+        const float4 uhi = make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.f);
         __stcg(tb.nbox + 2 * (int64_t)node, ulo);
         __stcg(tb.nbox + 2 * (int64_t)node + 1, uhi);
-        write_node(tb.nodes, node, cl[0], chh[0], ref[0], cnt[0], cl[1], chh[1], ref[1], cnt[1]);
+        write_node(tb.nodes, node, l0, h0, ref0, cnt0, l1, h1, ref1, cnt1);
         if (node == off) {  // Karras root: fill the root slot
             tb.rootbox[2 * m] = ulo;
             tb.rootbox[2 * m + 1] = uhi;
@@ -401,7 +406,12 @@ __global__ void k_climb(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ k
                 write_root(tb.nodes, root_slot, ulo, uhi, off, 0);
             return;
         }
-        node = tb.parent[node];
+        me = node;
+        mlo = ulo;
+        mhi = uhi;
+        mfirst = f0 < f1 ? f0 : f1;
+        msize = z0 + z1;
+        node = par;
     }
 }
 
