@@ -551,14 +551,4 @@ cudaError_t build_nodes4(const TreeBufs& tb, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int build_launches(const TreeBufs& tb, bool refit) {
-    if (tb.N == 0) return 0;
-    int np = 4;
-    for (int sh = 32; sh < 64 && ((int64_t)(tb.M - 1) >> (sh - 32)) > 0; sh += 8) ++np;
-    int k = refit ? 1 : (2 + 3 * np + 1);  // bounds, Morton, np x (hist, scan, scatter), Karras
-    k += 1;  // climb
-    if (tb.M == 1 && tb.top_levels > 0) k += 1;
-    return k;
-}
-
 }  // namespace rsi

@@ -64,11 +64,4 @@ cudaError_t segment_order(const float* A, const float* B, int n, const float4* r
     return e;
 }
 
-int segment_order_launches(int bits) {
-    const int pbits = (bits - 3) / 3;
-    int np = 0;
-    for (int sh = 0; sh < 3 * pbits + 3; sh += 8) ++np;
-    return 1 + 3 * np;
-}
-
 }  // namespace rsi

@@ -14,7 +14,4 @@ cudaError_t build_tree(TreeBufs& tb, const MeshArgs& ma, cudaStream_t s, bool re
 // Enqueue the 4-wide records of every slot (needs a completed build).
 cudaError_t build_nodes4(const TreeBufs& tb, cudaStream_t s);
 
-// Number of kernel launches build_tree enqueues.
-int build_launches(const TreeBufs& tb, bool refit);
-
 }  // namespace rsi

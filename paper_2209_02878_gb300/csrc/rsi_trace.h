@@ -66,7 +66,6 @@ struct SegOrderWs {
 // points into ws when the stream reaches it.
 cudaError_t segment_order(const float* A, const float* B, int n, const float4* rootbox, int bits,
                           SegOrderWs& ws, cudaStream_t s, const int32_t** order);
-int segment_order_launches(int bits);
 
 // Odd-parity classification helpers (inside.cu).
 cudaError_t launch_inside_segments(const float* P, int64_t n, const float4* rootbox, float* B,

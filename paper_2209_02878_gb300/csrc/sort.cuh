@@ -9,6 +9,8 @@
 //                  rank within the tile (each warp owns a contiguous run and
 //                  ranks equal digits with __match_any_sync in key order),
 //                  scatter to base + tile offset + rank.
+// With at most kSortFuseTiles tiles the scan kernel is skipped: every
+// scatter block sums the (few) tile histograms of its digit itself.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -82,7 +84,9 @@ static __global__ void __launch_bounds__(256) k_sort_scan(uint32_t* __restrict__
     if (threadIdx.x == 0) totals[blockIdx.x] = tot;
 }
 
-template <typename K, int ITEMS>
+constexpr int kSortFuseTiles = 64;
+
+template <typename K, int ITEMS, bool FUSED>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, int n, int shift, const uint32_t* __restrict__ hist,
@@ -91,8 +95,23 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     __shared__ uint32_t cnt[W][kSortBins];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int q = threadIdx.x; q < W * kSortBins; q += kSortThreads) (&cnt[0][0])[q] = 0;
+    // this tile's offset within digit d (FUSED: summed here from the raw tile
+    // histograms) and the digit total; kSortThreads == bins, thread = digit
+    uint32_t toff, dtot;
+    if (FUSED) {
+        const uint32_t* row = hist + (size_t)threadIdx.x * ntiles;
+        toff = dtot = 0u;
+        for (int q = 0; q < ntiles; ++q) {
+            const uint32_t x = row[q];
+            toff += q < (int)blockIdx.x ? x : 0u;
+            dtot += x;
+        }
+    } else {
+        toff = hist[threadIdx.x * ntiles + blockIdx.x];
+        dtot = totals[threadIdx.x];
+    }
     // digit base = exclusive scan of the digit totals
-    const uint32_t dbase = block_scan_u32(totals[threadIdx.x], nullptr);  // kSortThreads == bins
+    const uint32_t dbase = block_scan_u32(dtot, nullptr);
     const int wbase = blockIdx.x * (kSortThreads * ITEMS) + w * (32 * ITEMS);
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t local[ITEMS];
@@ -112,7 +131,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     __syncthreads();
     {
         const int d = threadIdx.x;
-        uint32_t run = dbase + hist[d * ntiles + blockIdx.x];
+        uint32_t run = dbase + toff;
 #pragma unroll
         for (int q = 0; q < W; ++q) {
             const uint32_t x = cnt[q][d];
@@ -149,10 +168,16 @@ static cudaError_t radix_sort_tiles(K* keys[2], uint32_t* vals[2], int n, const 
     for (int p = 0; p < np && n > 0; ++p) {
         k_sort_hist<K, ITEMS><<<ntiles, kSortThreads, 0, s>>>(keys[cur], n, shifts[p], hist,
                                                               ntiles);
-        k_sort_scan<<<kSortBins, 256, 0, s>>>(hist, ntiles, totals);
-        k_sort_scatter<K, ITEMS><<<ntiles, kSortThreads, 0, s>>>(
-            keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], n, shifts[p], hist, totals,
-            ntiles);
+        if (ntiles <= kSortFuseTiles) {
+            k_sort_scatter<K, ITEMS, true><<<ntiles, kSortThreads, 0, s>>>(
+                keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], n, shifts[p], hist, totals,
+                ntiles);
+        } else {
+            k_sort_scan<<<kSortBins, 256, 0, s>>>(hist, ntiles, totals);
+            k_sort_scatter<K, ITEMS, false><<<ntiles, kSortThreads, 0, s>>>(
+                keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], n, shifts[p], hist, totals,
+                ntiles);
+        }
         cur = 1 - cur;
     }
     *out = cur;
