@@ -477,6 +477,53 @@ def run_reference(args):
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def run_case(args):
+    """One secondary kernel on its workload, launched `--steps` times after
+    the warm-up, for a profiler capture (prints one JSON line with the mean
+    event-timed duration; not a benchmark result)."""
+    import numpy as np
+    import torch
+    import paper_2209_02878_gb300 as rsi
+    from paper_2209_02878_gb300 import synth
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.Stream()
+
+    def t(x):
+        return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+    with torch.cuda.stream(stream):
+        if args.case == "sphere_nearest":
+            mesh, seg = synth.workload_sphere()
+            bvh = rsi.BVH(t(mesh.V), t(mesh.T), stream=stream)
+            A, B = t(seg.A), t(seg.B)
+            o = bvh.intersect(A, B, "nearest", stream=stream)
+            fn = lambda: bvh.intersect(A, B, "nearest", out=o, stream=stream)  # noqa: E731
+        elif args.case == "coherent_packet":
+            mesh, seg = synth.workload_raster()
+            bvh = rsi.BVH(t(mesh.V), t(mesh.T), stream=stream)
+            A, B = t(seg.A), t(seg.B)
+            lo = {"packet": 1}
+            o = bvh.intersect(A, B, "nearest", launch=lo, stream=stream)
+            fn = lambda: bvh.intersect(A, B, "nearest", launch=lo, out=o, stream=stream)  # noqa: E731
+        elif args.case == "diff_backward":
+            mesh, seg, w = synth.workload_diff()
+            V, T, A, B, W = t(mesh.V), t(mesh.T), t(seg.A), t(seg.B), t(w)
+            tri = rsi.BVH(V, T, stream=stream).intersect(A, B, "nearest", stream=stream)["tri"]
+            gV = torch.zeros_like(V)
+            fn = lambda: rsi.intersect_backward(V, T, A, B, tri, grad_point=W, grad_V=gV,  # noqa: E731
+                                                stream=stream)
+        else:  # batched
+            items = synth.workload_batched()
+            tens = [(t(m.V), t(m.T), t(sg.A), t(sg.B), mode) for m, sg, mode in items]
+            b = rsi.Batch(tens, leaf_size=1, launch={"block_size": 128, "stack_depth": 64},
+                          stream=stream).build(stream=stream)
+            fn = lambda: b.intersect(stream=stream)  # noqa: E731
+        for _ in range(max(1, args.warmup)):
+            fn()
+        ms = timed(fn, args.steps, stream, torch)
+    print(json.dumps({"case": args.case, "launches": args.steps, "ms_per_launch": round(ms, 4)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -486,8 +533,13 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline workload only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly")
+    ap.add_argument("--case", choices=["sphere_nearest", "coherent_packet", "diff_backward",
+                                       "batched"],
+                    help="run one secondary kernel --steps times for a profiler capture")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
