@@ -294,10 +294,15 @@ rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR
  * the handle on first use from the device allocator, on s), so that the traversal of
  * one chunk and the copy of the previous chunk's results back overlap.
  * When hA and hB both lie in page-locked memory the device can address
- * (cudaHostAlloc / cudaHostRegister, unified addressing), the traversal
- * kernel reads the segments in place over the CPU-GPU link; otherwise each
- * chunk is first copied to the staging buffer, overlapped with the previous
- * chunk's traversal.  The work is ordered after everything already on s,
+ * (cudaHostAlloc / cudaHostRegister, unified addressing): in BOOL mode one
+ * persistent traversal starts at once while the copy engine streams the
+ * segments into device staging in chunks of `chunk` (0 -> 2^19, rounded up
+ * to 32) and flags each chunk as it lands, the warps waiting (bounded:
+ * RSI_ERR_TIMEOUT in the handle's status) for the chunks they take (25 B
+ * per segment of staging); in COUNT / NEAREST the traversal kernel reads
+ * the segments in place over the CPU-GPU link.  Otherwise each chunk is
+ * first copied to the staging buffer, overlapped with the previous chunk's
+ * traversal.  The work is ordered after everything already on s,
  * and s waits for it: the host outputs are complete once s is synchronised
  * (hA and hB must stay unchanged until then).  Pageable host memory is
  * staged by the driver and overlaps less.  Segments are processed in input
@@ -457,6 +462,15 @@ rsi_status rsi_autotune(rsi_bvh h, const float* dV, const int32_t* dT,
  * Synchronises s; allocates 4 bytes (device allocator, on s).  Errors:
  * RSI_ERR_ARG (iters < 1, tflops NULL), RSI_ERR_CUDA. */
 rsi_status rsi_fp32_peak(int64_t iters, double* tflops, rsi_stream s);
+
+/* Self-test of the bounded device-side wait (not part of the paper's
+ * method): one warp waits, with the wait the streamed host path uses, on a
+ * device flag that nothing sets; after `polls` polls (about 0.25 us each) it
+ * gives up and latches RSI_ERR_TIMEOUT into a status word, which is written
+ * to *status_out (host).  The context stays usable.  Synchronises s;
+ * allocates 8 bytes (device allocator, on s).  Errors: RSI_ERR_ARG
+ * (polls < 1, status_out NULL), RSI_ERR_OOM, RSI_ERR_CUDA. */
+rsi_status rsi_selftest_wait(int32_t polls, rsi_stream s, int32_t* status_out);
 
 #ifdef __cplusplus
 }

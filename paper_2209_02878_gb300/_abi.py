@@ -109,6 +109,7 @@ _PROTOS = {
                                P(rsi_tune_entry), i32, P(i32), P(rsi_launch_opts), P(i32)]),
     "rsi_fp32_peak": (C.c_int, [i64, P(C.c_double), vp]),
     "rsi_set_allocator": (C.c_int, [vp, vp, vp]),
+    "rsi_selftest_wait": (C.c_int, [i32, vp, P(i32)]),
 }
 
 # every entry point declared in include/rsi.h

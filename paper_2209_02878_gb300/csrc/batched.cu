@@ -42,6 +42,8 @@ __global__ void __maxnreg__(128) k_batch(BatchParams P) {
         C.S = 0;
         C.max_visits = P.max_visits;
         C.fetch = kFetchChunk;  // unused: each tile is one warp's whole pool
+        C.ready = nullptr;
+        C.ready_chunk = 1;
         C.order = nullptr;
         C.status = P.status;
         C.out = it.out;

@@ -51,6 +51,8 @@ __global__ void __maxnreg__(PacketRegs<MODE>::value) k_trace_packet(TraceParams 
     C.S = 0;
     C.max_visits = P.max_visits;
     C.fetch = 32;  // packets take 32 segments per warp themselves
+    C.ready = nullptr;
+    C.ready_chunk = 1;
     C.order = P.order;
     C.status = P.status;
     C.out = P.out;

@@ -1,3 +1,5 @@
+// Measurement and self-test utilities (not part of the paper's method).
+//
 // FP32 peak probe: the FP32 ceiling against which the traversal's box and
 // triangle arithmetic is compared (the traversal's own roofline is HBM
 // bandwidth nominally, issue rate in practice; this gives the third
@@ -32,7 +34,37 @@ __global__ void k_fma_probe(int64_t iters, float a, float b, float* sink) {
     if (s == -1.2345f) sink[0] = s;  // never true for the arguments used
 }
 
+// One warp waits on a flag that nothing sets, with the traversal's bounded
+// wait; the wait gives up after `polls` polls and latches the status.
+__global__ void k_wait_selftest(const int32_t* flag, int32_t* status, int polls) {
+    rsi::wait_flag(flag, status, polls);
+}
+
 }  // namespace
+
+extern "C" rsi_status rsi_selftest_wait(int32_t polls, rsi_stream s, int32_t* status_out) {
+    if (polls < 1 || !status_out) return RSI_ERR_ARG;
+    cudaStream_t cs = (cudaStream_t)s;
+    const rsi::AllocHooks hooks = rsi::current_hooks();
+    int32_t* mem = nullptr;  // [0] the flag, [1] the status word
+    if (rsi::dev_alloc(hooks, (void**)&mem, 2 * sizeof(int32_t), cs) != cudaSuccess) {
+        cudaGetLastError();
+        return RSI_ERR_OOM;
+    }
+    rsi_status st = RSI_OK;
+    if (cudaMemsetAsync(mem, 0, 2 * sizeof(int32_t), cs) != cudaSuccess) st = RSI_ERR_CUDA;
+    if (st == RSI_OK) {
+        k_wait_selftest<<<1, 32, 0, cs>>>(mem, mem + 1, polls);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(status_out, mem + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, cs) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(cs) != cudaSuccess)
+            st = RSI_ERR_CUDA;
+    }
+    rsi::dev_free(hooks, mem, cs);
+    if (st != RSI_OK) cudaGetLastError();
+    return st;
+}
 
 extern "C" rsi_status rsi_fp32_peak(int64_t iters, double* tflops, rsi_stream s) {
     if (iters < 1 || !tflops) return RSI_ERR_ARG;

@@ -35,6 +35,8 @@ struct TraceParams {
     unsigned long long* stats;  // 6 counters (STATS launches)
     int max_visits;             // node fetches per segment before giving up
     int fetch;                  // segments per warp fetch (set by launch_trace)
+    const int32_t* ready;       // streamed input flags (see TraceCtx), or nullptr
+    int64_t ready_chunk;
     const int32_t* order;       // optional coherent processing order (nullptr = identity)
     int32_t* status;
     TravOut out;

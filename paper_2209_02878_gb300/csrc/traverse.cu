@@ -43,6 +43,8 @@ __global__ void __maxnreg__(TraceRegs<MODE>::value) k_trace(TraceParams P) {
     C.S = S;
     C.max_visits = P.max_visits;
     C.fetch = P.fetch;
+    C.ready = P.ready;
+    C.ready_chunk = P.ready_chunk;
     C.order = P.order;
     C.status = P.status;
     C.out = P.out;

@@ -162,6 +162,8 @@ struct TraceCtx {
     int S;
     int max_visits;
     int fetch;             // segments a warp takes from the counter at once
+    const int32_t* ready;  // streamed input: chunk c of ready_chunk segments is in
+    int64_t ready_chunk;   // place once ready[c] != 0 (nullptr: all in place)
     const int32_t* order;  // optional processing order of the segments
     int32_t* status;
     TravOut out;
@@ -470,6 +472,24 @@ __device__ __forceinline__ void compact(const TravOut& o, bool has, int64_t i, c
 constexpr int kFetchChunk = 128;
 constexpr int kFetchMin = 32;
 constexpr int kRefillMin = 8;     // idle lanes that trigger a refill of a busy warp
+constexpr int kWaitPolls = 1 << 22;  // polls of a ready flag (~1 s) before RSI_ERR_TIMEOUT
+
+// Bounded wait of a whole warp for *flag != 0 (written by a copy on another
+// stream): every lane polls with an acquire load, so its later loads of the
+// flagged data are ordered after it.  Gives up after `polls` polls, latches
+// RSI_ERR_TIMEOUT and returns false (the caller carries on; its results are
+// then not to be trusted, which the status says).  Must be called by all 32
+// lanes.
+__device__ __forceinline__ bool wait_flag(const int32_t* flag, int32_t* status, int polls) {
+    for (int q = 0; q < polls; ++q) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (__all_sync(0xffffffffu, v != 0)) return true;
+        __nanosleep(256);
+    }
+    if ((threadIdx.x & 31) == 0) atomicCAS(status, 0, RSI_ERR_TIMEOUT);
+    return false;
+}
 
 // Persistent per-warp traversal loop over segments [lo, hi).  Every lane
 // holds one segment and advances it by one node per iteration; lanes whose
@@ -530,6 +550,9 @@ __device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long
                 }
                 pool = (int64_t)b;
                 pool_end = pool + C.fetch < hi ? pool + C.fetch : hi;
+                // streamed input: the chunks holding [pool, pool_end) have
+                // landed once the flag of the last one is set (copies in order)
+                if (C.ready) wait_flag(C.ready + (pool_end - 1) / C.ready_chunk, C.status, kWaitPolls);
             }
             const int64_t left = pool_end - pool;
             const int avail = left < (int64_t)__popc(idle) ? (int)left : __popc(idle);

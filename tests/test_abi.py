@@ -104,3 +104,6 @@ def test_argument_validation_without_gpu(lib):
     cb = _abi.ALLOC_FN(lambda n, d, s, c: None)
     assert L.rsi_set_allocator(ctypes.cast(cb, ctypes.c_void_p), None, None) == _abi.RSI_ERR_ARG
     assert L.rsi_set_allocator(None, None, None) == _abi.RSI_OK
+    st = ctypes.c_int32(0)
+    assert L.rsi_selftest_wait(0, None, ctypes.byref(st)) == _abi.RSI_ERR_ARG
+    assert L.rsi_selftest_wait(10, None, None) == _abi.RSI_ERR_ARG

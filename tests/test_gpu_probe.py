@@ -1,6 +1,8 @@
-"""rsi_fp32_peak, the FP32 ceiling the benchmark compares the traversal's
-arithmetic with: the measured rate must be plausible for the device (well
-above zero, not above its FP32 units at the maximum clock)."""
+"""Measurement and self-test entry points: rsi_fp32_peak, the FP32 ceiling
+the benchmark compares the traversal's arithmetic with (the measured rate
+must be plausible for the device: well above zero, not above its FP32 units
+at the maximum clock), and rsi_selftest_wait, the bounded device-side wait
+running out."""
 import pytest
 import torch
 
@@ -18,3 +20,23 @@ def test_fp32_peak_is_plausible():
     # the rate does not depend on the length of the run
     v2 = rsi.fp32_peak(1 << 17)
     assert abs(v2 - v) <= 0.15 * v, (v, v2)
+
+
+def test_bounded_wait_times_out_and_the_context_survives():
+    """The bounded wait that the streamed host path uses, on a flag that
+    nothing sets: it gives up, latches RSI_ERR_TIMEOUT, and the device is
+    still usable afterwards."""
+    import ctypes as C
+
+    from paper_2209_02878_gb300 import _abi, synth
+    lib = _abi.load()
+    st = C.c_int32(-1)
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.rsi_selftest_wait(2000, s, C.byref(st)) == _abi.RSI_OK
+    assert st.value == _abi.RSI_ERR_TIMEOUT
+    mesh, seg = synth.workload_small_bool()
+    dev = torch.device("cuda:0")
+    bvh = rsi.BVH(torch.from_numpy(mesh.V).to(dev), torch.from_numpy(mesh.T).to(dev))
+    flag = bvh.intersect(torch.from_numpy(seg.A).to(dev), torch.from_numpy(seg.B).to(dev))["flag"]
+    torch.cuda.synchronize()
+    assert bvh.status() == 0 and 0 < int(flag.sum()) < seg.n
