@@ -178,6 +178,10 @@ struct rsi_bvh_s {
     char* pipe_mem = nullptr;
     size_t pipe_bytes = 0;
     int32_t* one = nullptr;  // pinned host 1: the value of a streamed chunk's ready flag
+    // streamed path: the staging is free again once this event (recorded
+    // after the previous streamed call's traversal and copy back) completes
+    cudaEvent_t sev_free = nullptr, sev_reset = nullptr;
+    bool sfree_valid = false;
     cudaStream_t pipe_stream = nullptr;
     // odd-parity workspace (rsi_points_inside): segment ends + counts
     char* in_mem = nullptr;
@@ -374,6 +378,8 @@ rsi_status rsi_bvh_destroy(rsi_bvh h) {
         if (h->pev_done[q]) cudaEventDestroy(h->pev_done[q]);
     }
     if (h->pev_start) cudaEventDestroy(h->pev_start);
+    if (h->sev_free) cudaEventDestroy(h->sev_free);
+    if (h->sev_reset) cudaEventDestroy(h->sev_reset);
     if (h->one) cudaFreeHost(h->one);
     cudaError_t e = rsi::dev_free(h->hooks, h->mem, h->stream);
     if (cur != h->device) cudaSetDevice(cur);
@@ -560,8 +566,11 @@ static const float* mapped_host(const float* p, size_t bytes) {
 // internal stream and sets each chunk's ready flag by a 4-byte copy after
 // its data; a warp waits (bounded) for the flag of the chunk it takes
 // segments from.  The copy (~211 GB/s) and the traversal overlap instead of
-// one waiting for the other.  Staging: 24 B + 1 B per segment, held by the
-// handle.
+// one waiting for the other.  The copies wait only for the previous streamed
+// call to be done with the staging (not for everything on s), so they
+// overlap whatever precedes this call on s, e.g. the tree build; the flags
+// are reset on the copy stream and the traversal waits for that reset.
+// Staging: 24 B + 1 B per segment, held by the handle.
 static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB, int64_t nR,
                                      const rsi_output* hout, int64_t chunk,
                                      const rsi_launch_opts* lo, cudaStream_t cs) {
@@ -571,7 +580,13 @@ static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB
     const int64_t nc = (nR + ch - 1) / ch;
     const size_t ab = align256(12 * (size_t)nR), fb = align256((size_t)nR);
     const size_t need = 2 * ab + fb + align256(4 * (size_t)nc);
+    if (!h->sev_free) {
+        RSI_CK(cudaEventCreateWithFlags(&h->sev_free, cudaEventDisableTiming));
+        RSI_CK(cudaEventCreateWithFlags(&h->sev_reset, cudaEventDisableTiming));
+    }
+    bool fresh = false;  // staging (re)allocated on s: the copies must follow s
     if (h->pipe_bytes < need) {
+        fresh = true;
         if (h->pipe_mem) {
             RSI_CK(rsi::dev_free(h->hooks, h->pipe_mem, h->pipe_stream));
             h->pipe_mem = nullptr;
@@ -595,9 +610,14 @@ static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB
     uint8_t* dflag = (uint8_t*)(h->pipe_mem + 2 * ab);
     int32_t* ready = (int32_t*)(h->pipe_mem + 2 * ab + fb);
     cudaStream_t cp = h->pst[0];
-    RSI_CK(cudaMemsetAsync(ready, 0, 4 * (size_t)nc, cs));
-    RSI_CK(cudaEventRecord(h->pev_start, cs));
-    RSI_CK(cudaStreamWaitEvent(cp, h->pev_start, 0));
+    if (fresh || !h->sfree_valid) {
+        RSI_CK(cudaEventRecord(h->pev_start, cs));
+        RSI_CK(cudaStreamWaitEvent(cp, h->pev_start, 0));
+    } else {
+        RSI_CK(cudaStreamWaitEvent(cp, h->sev_free, 0));
+    }
+    RSI_CK(cudaMemsetAsync(ready, 0, 4 * (size_t)nc, cp));
+    RSI_CK(cudaEventRecord(h->sev_reset, cp));
     for (int64_t c = 0; c < nc; ++c) {
         const int64_t off = c * ch, n = nR - off < ch ? nR - off : ch;
         RSI_CK(cudaMemcpyAsync(dA + 3 * off, hA + 3 * off, 12 * (size_t)n, cudaMemcpyHostToDevice,
@@ -609,10 +629,14 @@ static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB
     rsi_output dout;
     memset(&dout, 0, sizeof(dout));
     dout.flag = dflag;
+    RSI_CK(cudaStreamWaitEvent(cs, h->sev_reset, 0));  // never the previous call's flags
+    h->sfree_valid = false;
     const rsi_status st = intersect_impl(h, dA, dB, nR, RSI_MODE_BOOL, &dout, lo, (rsi_stream)cs,
                                          false, nullptr, ready, ch);
     if (st != RSI_OK) return st;
     RSI_CK(cudaMemcpyAsync(hout->flag, dflag, (size_t)nR, cudaMemcpyDeviceToHost, cs));
+    RSI_CK(cudaEventRecord(h->sev_free, cs));
+    h->sfree_valid = true;
     RSI_CK(cudaEventRecord(h->pev_done[0], cp));
     RSI_CK(cudaStreamWaitEvent(cs, h->pev_done[0], 0));
     return RSI_OK;
@@ -664,6 +688,7 @@ rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64
         lo2.packet = 0;  // the packet kernel does not wait for streamed chunks
         return intersect_streamed(h, hA, hB, nR, hout, chunk, &lo2, cs);
     }
+    h->sfree_valid = false;  // this call uses the staging too: a later streamed call follows s
     // staging of buffer q: [A | B when copied] | outputs (flag / count /
     // tri, tuv, point, dist), each part 256-byte aligned
     const size_t in_b = in_place ? 0 : align256(12 * (size_t)ch);

@@ -367,3 +367,32 @@ def test_sphere_scale_count_nearest_sampled():
     out = (np.linalg.norm(seg.A, axis=1) > rmax) & (np.linalg.norm(seg.B, axis=1) > rmax)
     assert np.all(cnt[out] % 2 == 0)
     assert cnt.max() >= 4
+
+
+def test_host_calls_back_to_back(small):
+    """Streamed BOOL calls, in-place COUNT / NEAREST calls and rebuilds
+    queued on one stream without synchronising in between, with inputs of
+    different sizes: every result matches (the staging is shared, and a
+    streamed call's copies start as soon as the previous streamed call is
+    done with it)."""
+    mesh, seg, ref = small
+    V, T = dev(mesh.V), dev(mesh.T)
+    bvh = rsi.BVH(V, T)
+    A, B = torch.from_numpy(seg.A).pin_memory(), torch.from_numpy(seg.B).pin_memory()
+    n2 = 6007
+    A2, B2 = A[:n2].clone().pin_memory(), B[:n2].clone().pin_memory()
+    s = torch.cuda.Stream()
+    outs = []
+    for it in range(3):
+        bvh.build(V, T, stream=s)
+        outs.append(("bool", None, bvh.intersect_host(A, B, "bool", chunk=1024, stream=s)))
+        outs.append(("count", None, bvh.intersect_host(A, B, "count", stream=s)))
+        outs.append(("bool", n2, bvh.intersect_host(A2, B2, "bool", stream=s)))
+        outs.append(("nearest", n2, bvh.intersect_host(A2, B2, "nearest", stream=s)))
+        outs.append(("bool", None, bvh.intersect_host(A, B, "bool", chunk=4096, stream=s)))
+    s.synchronize()
+    for mode, n, o in outs:
+        sel = slice(None) if n is None else slice(0, n)
+        key = {"bool": "flag", "count": "count", "nearest": "tri"}[mode]
+        np.testing.assert_array_equal(o[key].numpy(), ref[key][sel], err_msg=f"{mode} n={n}")
+    assert bvh.status() == 0
