@@ -23,6 +23,12 @@
  *    prefix are host pointers.
  *  - rsi_stream is a cudaStream_t (NULL = legacy default stream).  Every
  *    compute call is asynchronous on that stream unless stated otherwise.
+ *  - A handle (rsi_bvh, rsi_batch) holds its tree, work counters,
+ *    workspaces and internal streams: calls on one handle must not run
+ *    concurrently from several host threads, and their GPU work must not
+ *    overlap -- queue them on one stream, or order the streams with events
+ *    (rsi_intersect_host orders its own internal streams).  Different
+ *    handles are independent.
  *  - Calls never throw, never abort and never trap the GPU; they return an
  *    rsi_status.  Errors that can only be seen on the device (a triangle index
  *    outside [0, nV)) are latched in a device status word and returned by
