@@ -32,7 +32,7 @@
  *  - Calls never throw, never abort and never trap the GPU; they return an
  *    rsi_status.  Errors that can only be seen on the device (a triangle index
  *    outside [0, nV)) are latched in a device status word and returned by
- *    rsi_bvh_status (which synchronises the stream).
+ *    rsi_bvh_status / rsi_batch_status (which synchronise the stream).
  *  - Arithmetic: FP32 with certified error bounds; every boolean decision
  *    whose FP32 error bound does not settle it is recomputed in FP64 in the
  *    exact operation order of the definition below, so flags, counts and
@@ -249,8 +249,10 @@ rsi_status rsi_build_bvh(const float* dV, int64_t nV, const int32_t* dT, int64_t
 rsi_status rsi_refit(rsi_bvh h, const float* dV, const int32_t* dT, rsi_stream s);
 
 /* Synchronise s and return the device-side status latched by builds and
- * traversals on h since the last call (RSI_OK, RSI_ERR_BAD_INDEX,
- * RSI_ERR_STACK_OVERFLOW), then clear it. */
+ * traversals on h since the last call (RSI_OK; RSI_ERR_BAD_INDEX: a triangle
+ * index outside [0, nV); RSI_ERR_INTERNAL: a traversal exceeded its visit
+ * bound, i.e. a corrupt tree; RSI_ERR_TIMEOUT: a streamed host call's wait
+ * for its data gave up), then clear it. */
 rsi_status rsi_bvh_status(rsi_bvh h, rsi_stream s);
 
 rsi_status rsi_bvh_get_info(rsi_bvh h, rsi_bvh_info* info);
@@ -430,6 +432,10 @@ rsi_status rsi_batch_intersect(rsi_batch b, rsi_stream s);
  * launch it; later calls replay the graph.  rebuild = 0 replays only the
  * traversal graph. */
 rsi_status rsi_batch_run_graph(rsi_batch b, int32_t rebuild, rsi_stream s);
+
+/* As rsi_bvh_status for a batch: synchronise s, return and clear the status
+ * latched by the batch's build and traversals. */
+rsi_status rsi_batch_status(rsi_batch b, rsi_stream s);
 
 rsi_status rsi_batch_destroy(rsi_batch b);
 

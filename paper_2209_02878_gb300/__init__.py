@@ -432,6 +432,10 @@ class Batch:
                    "rsi_batch_run_graph")
         return self.outputs
 
+    def status(self, stream=None) -> int:
+        """Synchronise and return (then clear) the batch's device-side status."""
+        return int(self._lib.rsi_batch_status(self._h, _stream(stream)))
+
     def close(self):
         if getattr(self, "_h", None):
             try:

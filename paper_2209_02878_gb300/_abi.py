@@ -85,6 +85,7 @@ _PROTOS = {
     "rsi_build_bvh": (C.c_int, [vp, i64, vp, i64, P(rsi_build_opts), vp, P(vp)]),
     "rsi_refit": (C.c_int, [vp, vp, vp, vp]),
     "rsi_bvh_status": (C.c_int, [vp, vp]),
+    "rsi_batch_status": (C.c_int, [vp, vp]),
     "rsi_bvh_get_info": (C.c_int, [vp, P(rsi_bvh_info)]),
     "rsi_bvh_destroy": (C.c_int, [vp]),
     "rsi_bvh_export": (C.c_int, [vp, vp] + [vp] * 9),

@@ -1029,6 +1029,16 @@ rsi_status rsi_batch_run_graph(rsi_batch b, int32_t rebuild, rsi_stream s) {
     return RSI_OK;
 }
 
+rsi_status rsi_batch_status(rsi_batch b, rsi_stream s) {
+    if (!b) return RSI_ERR_ARG;
+    int32_t v = 0;
+    RSI_CK(cudaMemcpyAsync(&v, b->tb.status, 4, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+    RSI_CK(cudaStreamSynchronize((cudaStream_t)s));
+    RSI_CK(cudaMemsetAsync(b->tb.status, 0, 4, (cudaStream_t)s));
+    RSI_CK(cudaStreamSynchronize((cudaStream_t)s));
+    return (rsi_status)v;
+}
+
 rsi_status rsi_batch_destroy(rsi_batch b) {
     if (!b) return RSI_ERR_ARG;
     if (b->g_full) cudaGraphExecDestroy(b->g_full);

@@ -98,6 +98,7 @@ def test_argument_validation_without_gpu(lib):
     assert L.rsi_intersect_host(None, None, None, 5, 0, ctypes.byref(out), 0, None,
                                 None) == _abi.RSI_ERR_ARG
     assert L.rsi_bvh_destroy(None) == _abi.RSI_ERR_ARG
+    assert L.rsi_batch_status(None, None) == _abi.RSI_ERR_ARG
     v = ctypes.c_double(0.0)
     assert L.rsi_fp32_peak(0, ctypes.byref(v), None) == _abi.RSI_ERR_ARG
     assert L.rsi_fp32_peak(10, None, None) == _abi.RSI_ERR_ARG

@@ -92,3 +92,28 @@ def test_autotune_returns_valid_config():
     ref = oracle.brute(mesh.V, mesh.T, seg.A, seg.B)
     got = bvh.intersect(A, B, "bool", launch=best)["flag"].cpu().numpy()
     np.testing.assert_array_equal(got, ref["flag"])
+
+
+def test_batched_full_size_sampled():
+    """The full 64-mesh workload (1k-200k triangles, 19.8M segments) in the
+    benchmark's configuration (one graph: multi-mesh build + persistent
+    traversal), 64 sampled segments per mesh against brute force."""
+    items = synth.workload_batched()
+    tens = [(dev(m.V), dev(m.T), dev(s.A), dev(s.B), mode) for m, s, mode in items]
+    assert sum(s.n for _, s, _ in items) > 10_000_000
+    b = rsi.Batch(tens, leaf_size=1, launch=dict(block_size=128, stack_depth=64))
+    outs = b.run_graph(rebuild=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(7)
+    for k, (mesh, seg, mode) in enumerate(items):
+        idx = np.sort(rng.choice(seg.n, min(64, seg.n), replace=False))
+        ref = oracle.brute(mesh.V, mesh.T, seg.A[idx], seg.B[idx])
+        if mode == "bool":
+            np.testing.assert_array_equal(outs[k]["flag"][idx].cpu().numpy(), ref["flag"],
+                                          err_msg=f"item {k}")
+        else:
+            np.testing.assert_array_equal(outs[k]["tri"][idx].cpu().numpy(), ref["tri"],
+                                          err_msg=f"item {k}")
+            assert_close(outs[k]["tuv"][idx].cpu().numpy(), ref["tuv"], what=f"item {k} tuv")
+    assert b.status() == 0
+    b.close()
