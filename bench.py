@@ -196,7 +196,12 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
 
     n_seg = 10_000_000
-    mesh, seg = synth.workload_paper_bool(seed=1 + 1000 * rank, n_seg=n_seg)
+    # every rank: the same (replicated) mesh; rank 0 the 10M segments of the
+    # single-GPU workload, rank r its own 10M of the same distribution
+    mesh, seg = synth.workload_paper_bool(n_seg=n_seg)
+    if rank > 0:
+        seg = synth.segments_random_direction(np.random.default_rng(1 + 1000 * rank), n_seg,
+                                              mesh.V)
     V = torch.from_numpy(mesh.V).to(dev)
     T = torch.from_numpy(mesh.T).to(dev)
     A = torch.from_numpy(seg.A).to(dev)
@@ -220,7 +225,7 @@ def run_ours(args):
         stream.synchronize()
         step = eager_step
         if not args.no_graph:
-            # the whole step (build + traversal, 18 kernels) as one CUDA graph
+            # the whole step (build + traversal, 13 kernels) as one CUDA graph
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, stream=stream):
                 eager_step()
