@@ -513,6 +513,12 @@ def run_case(args):
             lo = {"packet": 1}
             o = bvh.intersect(A, B, "nearest", launch=lo, stream=stream)
             fn = lambda: bvh.intersect(A, B, "nearest", launch=lo, out=o, stream=stream)  # noqa: E731
+        elif args.case == "diff_nearest":
+            mesh, seg, _ = synth.workload_diff()
+            bvh = rsi.BVH(t(mesh.V), t(mesh.T), stream=stream)
+            A, B = t(seg.A), t(seg.B)
+            o = bvh.intersect(A, B, "nearest", stream=stream)
+            fn = lambda: bvh.intersect(A, B, "nearest", out=o, stream=stream)  # noqa: E731
         elif args.case == "diff_backward":
             mesh, seg, w = synth.workload_diff()
             V, T, A, B, W = t(mesh.V), t(mesh.T), t(seg.A), t(seg.B), t(w)
@@ -541,8 +547,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline workload only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly")
-    ap.add_argument("--case", choices=["sphere_nearest", "coherent_packet", "diff_backward",
-                                       "batched"],
+    ap.add_argument("--case", choices=["sphere_nearest", "coherent_packet", "diff_nearest",
+                                       "diff_backward", "batched"],
                     help="run one secondary kernel --steps times for a profiler capture")
     args = ap.parse_args()
     if args.case:
