@@ -416,10 +416,12 @@ static __device__ __noinline__ int mt64(float ax_, float ay_, float az_, float b
 // componentwise magnitudes sum |x_i| (|y_j| |z_k| + |y_k| |z_j|) and gamma_10
 // (every term carries at most 8 roundings, 2 more cover the magnitudes'
 // own rounding), instead of the max-norm products and 2^-17 that decisions
-// use.  Returns the bound on max(|t~ - t|, |u~ - u|, |v~ - v|) and the FP32
-// values; +inf when det cannot be bounded away from zero.
+// use.  Returns the bound on |t~ - t| and, in euv, the bound on
+// max(|u~ - u|, |v~ - v|), with the FP32 values; +inf when det cannot be
+// bounded away from zero.
 __device__ __forceinline__ float mt32_tight(const Seg& s, const float4& A, const float4& B,
-                                           const float4& C, float& t, float& u, float& v) {
+                                           const float4& C, float& t, float& u, float& v,
+                                           float& euv) {
     const float e1x = B.x - A.x, e1y = B.y - A.y, e1z = B.z - A.z;
     const float e2x = C.x - A.x, e2y = C.y - A.y, e2z = C.z - A.z;
     const float sx = s.ax - A.x, sy = s.ay - A.y, sz = s.az - A.z;
@@ -443,6 +445,7 @@ __device__ __forceinline__ float mt32_tight(const Seg& s, const float4& A, const
     const float Bv = g * (fabsf(s.dx) * Qx + fabsf(s.dy) * Qy + fabsf(s.dz) * Qz) + kFilterEta;
     const float Bt = g * (fabsf(e2x) * Qx + fabsf(e2y) * Qy + fabsf(e2z) * Qz) + kFilterEta;
     const float ad = fabsf(det);
+    euv = INFINITY;
     if (!(ad > 2.f * Bd) || !isfinite(ad)) return INFINITY;
     const float inv = __frcp_rn(ad);
     const float sg = det < 0.f ? -1.f : 1.f;
@@ -454,7 +457,8 @@ __device__ __forceinline__ float mt32_tight(const Seg& s, const float4& A, const
     const float et = fmaf(fabsf(t), Bd, Bt) * den;
     const float eu = fmaf(fabsf(u), Bd, Bu) * den;
     const float ev = fmaf(fabsf(v), Bd, Bv) * den;
-    return fmaxf(fmaxf(et, eu), ev) * 1.001f + 0x1p-22f * fmaxf(1.f, fmaxf(fabsf(t), fmaxf(fabsf(u), fabsf(v))));
+    euv = fmaxf(eu, ev) * 1.001f + 0x1p-22f * fmaxf(1.f, fmaxf(fabsf(u), fabsf(v)));
+    return et * 1.001f + 0x1p-22f * fmaxf(1.f, fabsf(t));
 }
 
 // ---------------------------------------------------------------- double-float

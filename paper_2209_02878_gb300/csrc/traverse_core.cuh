@@ -356,10 +356,12 @@ __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, con
     t = res.bt;
     u = res.bu;
     v = res.bv;
-    // the tolerance of these outputs is 1e-5 (of the point too, which moves by
-    // |d| times the error of t); the bounds are rigorous, keep a margin of 2
+    // the tolerance of these outputs is 1e-5 (the bounds are rigorous, keep a
+    // margin of 2): t needs 5e-6 / |d| (the point and the distance move by
+    // |d| times the error of t), u and v 5e-6
     const float dlen = sqrtf(fmaf(s.dx, s.dx, fmaf(s.dy, s.dy, s.dz * s.dz))) * 1.0001f;
     const float thresh = 5e-6f / fmaxf(1.f, dlen);
+    const float thresh_uv = 5e-6f;
     const int p = res.bpos;
     if (s.fp64only) {
         if (STATS) ++st.refines;
@@ -379,12 +381,12 @@ __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, con
         dist = (float)(tuv[0] * sqrt(dd));
         return;
     }
-    bool refine = res.berr > thresh;
-    if (refine) {  // a tighter bound for this one triangle first
-        float t2, u2, v2;
-        const float e = mt32_tight(s, ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
-                                   ld4(tris + 3 * (int64_t)p + 2), t2, u2, v2);
-        if (e <= thresh) {
+    bool refine = res.berr > thresh;  // berr bounds t, u and v together
+    if (refine) {  // tighter bounds for this one triangle first, t and (u, v) apart
+        float t2, u2, v2, euv;
+        const float et = mt32_tight(s, ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
+                                    ld4(tris + 3 * (int64_t)p + 2), t2, u2, v2, euv);
+        if (et <= thresh && euv <= thresh_uv) {
             t = t2;
             u = u2;
             v = v2;
