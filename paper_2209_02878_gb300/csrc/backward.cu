@@ -8,17 +8,39 @@
 //     dL/da = (1-t)(gP + lambda),  dL/db = t (gP + lambda),
 //     dL/dv0 = -(1-u-v) lambda, dL/dv1 = -u lambda, dL/dv2 = -v lambda.
 // One thread per segment; vertex gradients are scattered with atomicAdd
-// (the only cross-segment reduction).  The per-segment algebra and the
-// vertex accumulation run in FP64 -- (t, u, v) recomputed from the geometry
-// as in the definition -- because a vertex gradient is a sum of a few
-// contributions that can cancel, and FP32 atomics would leave an absolute
-// error proportional to the sum of their magnitudes; the total is rounded
-// to FP32 once.
+// (the only cross-segment reduction).  The per-segment algebra runs in
+// double-float (pairs of floats from the error-free transformations, about
+// 44 significant bits: the input differences are exact, (t, u, v) are
+// recomputed from the geometry as in the definition) -- GB300's FP64 rate is
+// a small fraction of its FP32 rate and the FP64 version of this kernel kept
+// its FP64 pipe 83 % busy -- and the vertex accumulation in FP64 atomics
+// (done in L2), because a vertex gradient is a sum of a few contributions
+// that can cancel; the total is rounded to FP32 once.
 #include <cuda_runtime.h>
 
 #include "rsi_trace.h"
 
 namespace rsi {
+
+namespace {
+
+__device__ __forceinline__ dfl df_from(float x) { return {x, 0.f}; }
+
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ void df_cross(const dfl* x, const dfl* y, dfl* r) {
+    r[0] = df_sub(df_mul(x[1], y[2]), df_mul(x[2], y[1]));
+    r[1] = df_sub(df_mul(x[2], y[0]), df_mul(x[0], y[2]));
+    r[2] = df_sub(df_mul(x[0], y[1]), df_mul(x[1], y[0]));
+}
+
+__device__ __forceinline__ dfl df_dot(const dfl* x, const dfl* y) {
+    return df_add(df_add(df_mul(x[0], y[0]), df_mul(x[1], y[1])), df_mul(x[2], y[2]));
+}
+
+__device__ __forceinline__ double df_double(dfl a) { return (double)a.h + (double)a.l; }
+
+}  // namespace
 
 __global__ void k_backward(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ T,
                            int64_t nT, const float* __restrict__ A, const float* __restrict__ B,
@@ -29,64 +51,65 @@ __global__ void k_backward(const float* __restrict__ V, int64_t nV, const int32_
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nR) return;
     const int j = tri[i];
-    double ga[3] = {0.0, 0.0, 0.0}, gb[3] = {0.0, 0.0, 0.0};
+    float ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
     if (j >= 0 && j < nT) {
         const int64_t i0 = T[3 * (int64_t)j], i1 = T[3 * (int64_t)j + 1], i2 = T[3 * (int64_t)j + 2];
         if (i0 >= 0 && i0 < nV && i1 >= 0 && i1 < nV && i2 >= 0 && i2 < nV) {
-            double d[3], e1[3], e2[3], s0[3], nd[3];
+            dfl d[3], nd[3], e1[3], e2[3], s0[3];
             for (int k = 0; k < 3; ++k) {
-                const double a = A[3 * i + k], v0 = V[3 * i0 + k];
-                d[k] = (double)B[3 * i + k] - a;
-                nd[k] = -d[k];
-                e1[k] = (double)V[3 * i1 + k] - v0;
-                e2[k] = (double)V[3 * i2 + k] - v0;
-                s0[k] = a - v0;
+                const float a = A[3 * i + k], v0 = V[3 * i0 + k];
+                d[k] = df_two_sum(B[3 * i + k], -a);
+                nd[k] = df_neg(d[k]);
+                e1[k] = df_two_sum(V[3 * i1 + k], -v0);
+                e2[k] = df_two_sum(V[3 * i2 + k], -v0);
+                s0[k] = df_two_sum(a, -v0);
             }
-            const double c12[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
-                                   e1[0] * e2[1] - e1[1] * e2[0]};
-            const double c20[3] = {e2[1] * nd[2] - e2[2] * nd[1], e2[2] * nd[0] - e2[0] * nd[2],
-                                   e2[0] * nd[1] - e2[1] * nd[0]};
-            const double c01[3] = {nd[1] * e1[2] - nd[2] * e1[1], nd[2] * e1[0] - nd[0] * e1[2],
-                                   nd[0] * e1[1] - nd[1] * e1[0]};
-            const double detM = nd[0] * c12[0] + nd[1] * c12[1] + nd[2] * c12[2];
-            if (detM != 0.0) {
+            dfl c12[3], c20[3], c01[3];
+            df_cross(e1, e2, c12);
+            df_cross(e2, nd, c20);
+            df_cross(nd, e1, c01);
+            const dfl detM = df_dot(nd, c12);
+            if (detM.h != 0.f && isfinite(detM.h)) {
                 // x = M^-1 (a - v0): the rows of M^-1 are c12, c20, c01 over det M
-                const double inv = 1.0 / detM;
-                const double t = (c12[0] * s0[0] + c12[1] * s0[1] + c12[2] * s0[2]) * inv;
-                const double u = (c20[0] * s0[0] + c20[1] * s0[1] + c20[2] * s0[2]) * inv;
-                const double v = (c01[0] * s0[0] + c01[1] * s0[1] + c01[2] * s0[2]) * inv;
-                double gp[3] = {0.0, 0.0, 0.0};
+                const float r = rcp_approx(detM.h);
+                const dfl t = df_div(df_dot(c12, s0), detM, r);
+                const dfl u = df_div(df_dot(c20, s0), detM, r);
+                const dfl v = df_div(df_dot(c01, s0), detM, r);
+                float gp[3] = {0.f, 0.f, 0.f};
                 if (gP) {
                     gp[0] = gP[3 * i];
                     gp[1] = gP[3 * i + 1];
                     gp[2] = gP[3 * i + 2];
                 }
-                double gx0 = gp[0] * d[0] + gp[1] * d[1] + gp[2] * d[2];
-                double gx1 = 0.0, gx2 = 0.0;
+                const dfl gpd[3] = {df_from(gp[0]), df_from(gp[1]), df_from(gp[2])};
+                dfl gx0 = df_dot(gpd, d), gx1 = df_from(0.f), gx2 = df_from(0.f);
                 if (gtuv) {
-                    gx0 += gtuv[3 * i];
-                    gx1 = gtuv[3 * i + 1];
-                    gx2 = gtuv[3 * i + 2];
+                    gx0 = df_add(gx0, df_from(gtuv[3 * i]));
+                    gx1 = df_from(gtuv[3 * i + 1]);
+                    gx2 = df_from(gtuv[3 * i + 2]);
                 }
-                const double w = 1.0 - u - v;
+                const dfl w = df_sub(df_sub(df_from(1.f), u), v);
+                const dfl omt = df_sub(df_from(1.f), t);
                 for (int k = 0; k < 3; ++k) {
-                    const double lam = (gx0 * c12[k] + gx1 * c20[k] + gx2 * c01[k]) * inv;
-                    const double sk = gp[k] + lam;
-                    ga[k] = (1.0 - t) * sk;
-                    gb[k] = t * sk;
+                    const dfl num =
+                        df_add(df_add(df_mul(gx0, c12[k]), df_mul(gx1, c20[k])), df_mul(gx2, c01[k]));
+                    const dfl lam = df_div(num, detM, r);
+                    const dfl sk = df_add(gpd[k], lam);
+                    ga[k] = df_float(df_mul(omt, sk));
+                    gb[k] = df_float(df_mul(t, sk));
                     if (gV64) {
-                        atomicAdd(gV64 + 3 * i0 + k, -w * lam);
-                        atomicAdd(gV64 + 3 * i1 + k, -u * lam);
-                        atomicAdd(gV64 + 3 * i2 + k, -v * lam);
+                        atomicAdd(gV64 + 3 * i0 + k, -df_double(df_mul(w, lam)));
+                        atomicAdd(gV64 + 3 * i1 + k, -df_double(df_mul(u, lam)));
+                        atomicAdd(gV64 + 3 * i2 + k, -df_double(df_mul(v, lam)));
                     }
                 }
             }
         }
     }
     if (gA)
-        for (int k = 0; k < 3; ++k) gA[3 * i + k] = (float)ga[k];
+        for (int k = 0; k < 3; ++k) gA[3 * i + k] = ga[k];
     if (gB)
-        for (int k = 0; k < 3; ++k) gB[3 * i + k] = (float)gb[k];
+        for (int k = 0; k < 3; ++k) gB[3 * i + k] = gb[k];
 }
 
 // dGradV += the FP64 accumulator, rounded once.
