@@ -248,11 +248,14 @@ class BVH:
 
     def intersect_host(self, A, B, mode="bool", *, out=None, chunk=0, launch=None,
                        stream=None):
-        """Test segments held in HOST memory (float32 [nR,3] CPU tensors; pin
-        them for overlap) with the chunked copy / traverse / copy-back
-        pipeline of rsi_intersect_host.  Returns a dict of host output
-        tensors (pinned when allocated here), complete once `stream` (default
-        current) is synchronised."""
+        """Test segments held in HOST memory (float32 [nR,3] CPU tensors) with
+        rsi_intersect_host: pinned inputs are streamed to the device under
+        one running traversal (BOOL) or read in place by the kernel (COUNT,
+        NEAREST); pageable ones go through chunked copies.  `chunk` sets the
+        copy / launch chunk in segments (0: the library's choice).  Returns a
+        dict of host output tensors (pinned when allocated here), complete
+        once `stream` (default current) is synchronised; A and B must stay
+        unchanged until then."""
         for t, nme in ((A, "A"), (B, "B")):
             if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32 or \
                     t.dim() != 2 or t.shape[1] != 3 or not t.is_contiguous():

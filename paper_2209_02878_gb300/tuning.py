@@ -36,9 +36,11 @@ def _load(path):
 
 def autotune(bvh, V, T, A, B, mode="bool", block_sizes=(64, 128, 256, 512),
              stack_depths=(8, 32, 64), smem_nodes=(-1, 255, 511, 1023), leaf_sizes=(1, 2, 4),
-             reps=5, cache: str | None = DEFAULT_CACHE, stream=None):
+             reps=5, cache: str | None = DEFAULT_CACHE, stream=None, try_packet=True):
     """Time every combination (the handle is rebuilt per leaf size) and
     return (best launch options dict, best leaf size, table of entries).
+    With try_packet, the warp-cooperative traversal (launch option `packet`,
+    faster when the segments are coherent) is timed against the winner too.
     The handle is left built with the best leaf size."""
     lib = _abi.load()
     m = _mode(mode)
@@ -72,6 +74,25 @@ def autotune(bvh, V, T, A, B, mode="bool", block_sizes=(64, 128, 256, 512),
     launch = dict(block_size=best.block_size, stack_depth=best.stack_depth,
                   smem_nodes=best.smem_nodes)
     bvh.leaf_size = best_leaf.value
+    if try_packet:
+        s = stream if stream is not None else torch.cuda.current_stream()
+
+        def median_ms(lo):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            bvh.intersect(A, B, m, launch=lo, out=o, stream=s)  # warm-up
+            ms = []
+            for _ in range(max(1, int(reps))):
+                e0.record(s)
+                bvh.intersect(A, B, m, launch=lo, out=o, stream=s)
+                e1.record(s)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return sorted(ms)[len(ms) // 2]
+
+        t_best, t_packet = median_ms(launch), median_ms({"packet": 1})
+        rows.append(dict(packet=1, leaf_size=best_leaf.value, ms=t_packet))
+        if t_packet < t_best:
+            launch = {"packet": 1}
     if cache:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         data = _load(cache)

@@ -87,8 +87,9 @@ def test_autotune_returns_valid_config():
     best, leaf, table = tuning.autotune(bvh, V, T, A, B, "bool", block_sizes=(128, 256),
                                         stack_depths=(8, 64), smem_nodes=(-1, 511),
                                         leaf_sizes=(1, 4), reps=3, cache=None)
-    assert len(table) == 16
-    assert best["block_size"] in (128, 256) and leaf in (1, 4)
+    assert len(table) == 16 + 1  # the grid, then the packet traversal
+    assert table[-1].get("packet") == 1 and leaf in (1, 4)
+    assert best == {"packet": 1} or best["block_size"] in (128, 256)
     ref = oracle.brute(mesh.V, mesh.T, seg.A, seg.B)
     got = bvh.intersect(A, B, "bool", launch=best)["flag"].cpu().numpy()
     np.testing.assert_array_equal(got, ref["flag"])
