@@ -128,18 +128,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// Per-segment registers of the traversal.
-struct Seg {
-    float ax, ay, az;  // start a
-    float dx, dy, dz;  // d = fl(b - a)
-    float ix, iy, iz;  // 1 / d (IEEE; +-inf for a zero component)
-    float md;          // max |d_i|
-    bool tiny;         // some 0 < |d_i| < 2^-60: boxes tested by overlap instead
-    bool fp64only;     // |d| outside the FP32 filter's range: decide in FP64
-    unsigned long long pax, pay, paz;  // (a_k, a_k) packed for f32x2 arithmetic
-    unsigned long long pix, piy, piz;  // (1/d_k, 1/d_k) packed
-};
-
 // Packed pairs of floats for the f32x2 instructions (one instruction computes
 // the same operation for both children of a node).
 __device__ __forceinline__ unsigned long long pk2(float a, float b) {
@@ -152,6 +140,31 @@ __device__ __forceinline__ float2 up2(unsigned long long r) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
     return v;
 }
+__device__ __forceinline__ float lo32(unsigned long long r) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    return a;
+}
+
+// Per-segment registers of the traversal.  Each endpoint and reciprocal
+// coordinate is held once, duplicated in both halves of a packed pair for the
+// f32x2 box test; the scalar accessors read the low half, so the register pair
+// serves both uses.
+struct Seg {
+    unsigned long long pax, pay, paz;  // (a_k, a_k): start a, packed for f32x2 arithmetic
+    unsigned long long pix, piy, piz;  // (1/d_k, 1/d_k) (IEEE; +-inf for a zero component)
+    float dx, dy, dz;  // d = fl(b - a)
+    float md;          // max |d_i|
+    bool tiny;         // some 0 < |d_i| < 2^-60: boxes tested by overlap instead
+    bool fp64only;     // |d| outside the FP32 filter's range: decide in FP64
+    __device__ __forceinline__ float ax() const { return lo32(pax); }
+    __device__ __forceinline__ float ay() const { return lo32(pay); }
+    __device__ __forceinline__ float az() const { return lo32(paz); }
+    __device__ __forceinline__ float ix() const { return lo32(pix); }
+    __device__ __forceinline__ float iy() const { return lo32(piy); }
+    __device__ __forceinline__ float iz() const { return lo32(piz); }
+};
+
 __device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
     unsigned long long r;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
@@ -167,7 +180,6 @@ __device__ __forceinline__ bool seg_setup(const float* A, const float* B, int64_
     const float ax = A[3 * i], ay = A[3 * i + 1], az = A[3 * i + 2];
     const float bx = B[3 * i], by = B[3 * i + 1], bz = B[3 * i + 2];
     if (!(finite3(ax, ay, az) && finite3(bx, by, bz))) return false;
-    s.ax = ax; s.ay = ay; s.az = az;
     s.dx = __fsub_rn(bx, ax);
     s.dy = __fsub_rn(by, ay);
     s.dz = __fsub_rn(bz, az);
@@ -175,9 +187,7 @@ __device__ __forceinline__ bool seg_setup(const float* A, const float* B, int64_
     // then never culls (conservative) and every decision is taken in FP64.
     // The reciprocal may be off by 1 ulp (PTX rcp.approx): the slab test's
     // slack covers it.
-    s.ix = rcp_approx(s.dx);
-    s.iy = rcp_approx(s.dy);
-    s.iz = rcp_approx(s.dz);
+    const float ix = rcp_approx(s.dx), iy = rcp_approx(s.dy), iz = rcp_approx(s.dz);
     s.md = maxabs3(s.dx, s.dy, s.dz);
     const float mn = fminf(fminf(s.dx != 0.f ? fabsf(s.dx) : 1.f, s.dy != 0.f ? fabsf(s.dy) : 1.f),
                            s.dz != 0.f ? fabsf(s.dz) : 1.f);
@@ -186,9 +196,9 @@ __device__ __forceinline__ bool seg_setup(const float* A, const float* B, int64_
     s.pax = pk2(ax, ax);
     s.pay = pk2(ay, ay);
     s.paz = pk2(az, az);
-    s.pix = pk2(s.ix, s.ix);
-    s.piy = pk2(s.iy, s.iy);
-    s.piz = pk2(s.iz, s.iz);
+    s.pix = pk2(ix, ix);
+    s.piy = pk2(iy, iy);
+    s.piz = pk2(iz, iz);
     return true;
 }
 
@@ -206,21 +216,21 @@ __device__ __forceinline__ bool slab(const Seg& s, float lx, float ly, float lz,
         // box-overlap test of the segment's own box; a + fl(b - a) is within
         // 3u (|a| + |b|) of b, so the box is padded by 2^-21 (|a| + |a + d|)
         tent = 0.f;
-        const float bx = s.ax + s.dx, by = s.ay + s.dy, bz = s.az + s.dz;
-        const float px = (fabsf(s.ax) + fabsf(bx)) * 0x1p-21f + 0x1p-140f;
-        const float py = (fabsf(s.ay) + fabsf(by)) * 0x1p-21f + 0x1p-140f;
-        const float pz = (fabsf(s.az) + fabsf(bz)) * 0x1p-21f + 0x1p-140f;
-        return !(fmaxf(s.ax, bx) + px < lx || fminf(s.ax, bx) - px > hx ||
-                 fmaxf(s.ay, by) + py < ly || fminf(s.ay, by) - py > hy ||
-                 fmaxf(s.az, bz) + pz < lz || fminf(s.az, bz) - pz > hz);
+        const float bx = s.ax() + s.dx, by = s.ay() + s.dy, bz = s.az() + s.dz;
+        const float px = (fabsf(s.ax()) + fabsf(bx)) * 0x1p-21f + 0x1p-140f;
+        const float py = (fabsf(s.ay()) + fabsf(by)) * 0x1p-21f + 0x1p-140f;
+        const float pz = (fabsf(s.az()) + fabsf(bz)) * 0x1p-21f + 0x1p-140f;
+        return !(fmaxf(s.ax(), bx) + px < lx || fminf(s.ax(), bx) - px > hx ||
+                 fmaxf(s.ay(), by) + py < ly || fminf(s.ay(), by) - py > hy ||
+                 fmaxf(s.az(), bz) + pz < lz || fminf(s.az(), bz) - pz > hz);
     }
-    const bool nx = s.ix < 0.f, ny = s.iy < 0.f, nz = s.iz < 0.f;
-    const float tnx = (__fsub_rn(nx ? hx : lx, s.ax)) * s.ix;
-    const float tfx = (__fsub_rn(nx ? lx : hx, s.ax)) * s.ix;
-    const float tny = (__fsub_rn(ny ? hy : ly, s.ay)) * s.iy;
-    const float tfy = (__fsub_rn(ny ? ly : hy, s.ay)) * s.iy;
-    const float tnz = (__fsub_rn(nz ? hz : lz, s.az)) * s.iz;
-    const float tfz = (__fsub_rn(nz ? lz : hz, s.az)) * s.iz;
+    const bool nx = s.ix() < 0.f, ny = s.iy() < 0.f, nz = s.iz() < 0.f;
+    const float tnx = (__fsub_rn(nx ? hx : lx, s.ax())) * s.ix();
+    const float tfx = (__fsub_rn(nx ? lx : hx, s.ax())) * s.ix();
+    const float tny = (__fsub_rn(ny ? hy : ly, s.ay())) * s.iy();
+    const float tfy = (__fsub_rn(ny ? ly : hy, s.ay())) * s.iy();
+    const float tnz = (__fsub_rn(nz ? hz : lz, s.az())) * s.iz();
+    const float tfz = (__fsub_rn(nz ? lz : hz, s.az())) * s.iz();
     const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, 0.f));
     const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tlim));
     tent = tn;
@@ -244,7 +254,7 @@ __device__ __forceinline__ void slab2(const Seg& s, const ulonglong2& q0, const 
         h1 = slab(s, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, tlim, t1);
         return;
     }
-    const bool nx = s.ix < 0.f, ny = s.iy < 0.f, nz = s.iz < 0.f;
+    const bool nx = s.ix() < 0.f, ny = s.iy() < 0.f, nz = s.iz() < 0.f;
     const float2 tnx = up2(mul2(sub2(nx ? hix : lox, s.pax), s.pix));
     const float2 tfx = up2(mul2(sub2(nx ? lox : hix, s.pax), s.pix));
     const float2 tny = up2(mul2(sub2(ny ? hiy : loy, s.pay), s.piy));
@@ -299,7 +309,7 @@ __device__ __forceinline__ int mt32(const Seg& s, const float4& A, const float4&
     const float m2 = maxabs3(e2x, e2y, e2z);
     // An exactly zero edge makes det exactly zero in FP64 too: never a hit.
     if (m1 == 0.f || m2 == 0.f) return 0;
-    const float sx = s.ax - A.x, sy = s.ay - A.y, sz = s.az - A.z;
+    const float sx = s.ax() - A.x, sy = s.ay() - A.y, sz = s.az() - A.z;
     const float ms = maxabs3(sx, sy, sz);
     const float mhi = fmaxf(fmaxf(m1, m2), ms);
     const float mlo = fminf(fminf(m1, m2), ms == 0.f ? 1.f : ms);
@@ -424,7 +434,7 @@ __device__ __forceinline__ float mt32_tight(const Seg& s, const float4& A, const
                                            float& euv) {
     const float e1x = B.x - A.x, e1y = B.y - A.y, e1z = B.z - A.z;
     const float e2x = C.x - A.x, e2y = C.y - A.y, e2z = C.z - A.z;
-    const float sx = s.ax - A.x, sy = s.ay - A.y, sz = s.az - A.z;
+    const float sx = s.ax() - A.x, sy = s.ay() - A.y, sz = s.az() - A.z;
     const float px = s.dy * e2z - s.dz * e2y, py = s.dz * e2x - s.dx * e2z;
     const float pz = s.dx * e2y - s.dy * e2x;
     const float qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;

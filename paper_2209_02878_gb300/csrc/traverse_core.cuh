@@ -395,7 +395,7 @@ __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, con
     }
     if (refine) {
         if (STATS) ++st.refines;
-        const float a3[3] = {s.ax, s.ay, s.az};
+        const float a3[3] = {s.ax(), s.ay(), s.az()};
         const float b3[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
         float tuv[3];
         mt_df(a3, b3, ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
@@ -404,9 +404,9 @@ __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, con
         u = tuv[1];
         v = tuv[2];
     }
-    P[0] = fmaf(t, s.dx, s.ax);
-    P[1] = fmaf(t, s.dy, s.ay);
-    P[2] = fmaf(t, s.dz, s.az);
+    P[0] = fmaf(t, s.dx, s.ax());
+    P[1] = fmaf(t, s.dy, s.ay());
+    P[2] = fmaf(t, s.dz, s.az());
     dist = t * sqrtf(fmaf(s.dx, s.dx, fmaf(s.dy, s.dy, s.dz * s.dz)));
 }
 
