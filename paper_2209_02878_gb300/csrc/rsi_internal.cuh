@@ -143,6 +143,7 @@ __device__ __forceinline__ float2 up2(unsigned long long r) {
 __device__ __forceinline__ float lo32(unsigned long long r) {
     float a, b;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    (void)b;
     return a;
 }
 

@@ -20,7 +20,7 @@ struct TraceRegs {
     static constexpr int value = MODE == RSI_MODE_BOOL ? 64 : (MODE == RSI_MODE_COUNT ? 72 : 80);
 };
 
-template <int MODE, int STACK, bool STATS, int W>
+template <int MODE, int STACK, bool STATS, int W, bool TL>
 __global__ void __maxnreg__(TraceRegs<MODE>::value) k_trace(TraceParams P) {
     extern __shared__ float4 snodes[];
     int S = 0;
@@ -50,31 +50,40 @@ __global__ void __maxnreg__(TraceRegs<MODE>::value) k_trace(TraceParams P) {
     C.out = P.out;
     TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull};
     unsigned long long segs = 0;
-    trace_loop<MODE, STACK, STATS, W>(C, P.work, 0, P.nR, st, segs);
+    trace_loop<MODE, STACK, STATS, W, TL>(C, P.work, 0, P.nR, st, segs);
     if (STATS) flush_stats(st, P.stats, segs);
 }
 
 using KernelFn = void (*)(TraceParams);
 
-template <int MODE, bool STATS, int W>
+template <int MODE, bool STATS, int W, bool TL>
 static KernelFn pick_stack(int stack) {
     switch (stack) {
-        case 8: return k_trace<MODE, 8, STATS, W>;
-        case 32: return k_trace<MODE, 32, STATS, W>;
-        default: return k_trace<MODE, 64, STATS, W>;
+        case 8: return k_trace<MODE, 8, STATS, W, TL>;
+        case 32: return k_trace<MODE, 32, STATS, W, TL>;
+        default: return k_trace<MODE, 64, STATS, W, TL>;
     }
 }
 
-template <bool STATS, int W>
+// Without a treelet, BOOL and COUNT take the variant with the treelet tests
+// compiled out (1-2 % faster on the paper-scale heightfield); binary NEAREST
+// always takes the general one, which the register allocator handles better
+// (2.22 against 2.39 ms there).
+template <bool STATS, int W, bool TL>
 static KernelFn pick_mode(int mode, int stack) {
-    if (mode == RSI_MODE_BOOL) return pick_stack<RSI_MODE_BOOL, STATS, W>(stack);
-    if (mode == RSI_MODE_COUNT) return pick_stack<RSI_MODE_COUNT, STATS, W>(stack);
-    return pick_stack<RSI_MODE_NEAREST, STATS, W>(stack);
+    if (mode == RSI_MODE_BOOL) return pick_stack<RSI_MODE_BOOL, STATS, W, TL>(stack);
+    if (mode == RSI_MODE_COUNT) return pick_stack<RSI_MODE_COUNT, STATS, W, TL>(stack);
+    return pick_stack<RSI_MODE_NEAREST, STATS, W, TL || W == 2>(stack);
 }
 
-KernelFn trace_kernel(int mode, int stack, bool stats, int width) {
-    if (width == 2) return stats ? pick_mode<true, 2>(mode, stack) : pick_mode<false, 2>(mode, stack);
-    return stats ? pick_mode<true, 4>(mode, stack) : pick_mode<false, 4>(mode, stack);
+// The treelet variant for binary traversal from a treelet root (~0); 4-wide
+// traversal starts at the global root.
+KernelFn trace_kernel(int mode, int stack, bool stats, int width, bool treelet) {
+    if (width != 2)
+        return stats ? pick_mode<true, 4, false>(mode, stack) : pick_mode<false, 4, false>(mode, stack);
+    if (treelet)
+        return stats ? pick_mode<true, 2, true>(mode, stack) : pick_mode<false, 2, true>(mode, stack);
+    return stats ? pick_mode<true, 2, false>(mode, stack) : pick_mode<false, 2, false>(mode, stack);
 }
 
 struct OccKey {
@@ -138,7 +147,7 @@ int max_block(const void* fn, int block) {
 
 cudaError_t launch_trace(const TraceParams& P, int mode, int stack, bool stats, int block,
                          int width, cudaStream_t s) {
-    KernelFn fn = trace_kernel(mode, stack, stats, width);
+    KernelFn fn = trace_kernel(mode, stack, stats, width, P.root < 0);
     block = max_block((const void*)fn, block);  // register-limited kernels cap the block
     const int smem = P.smem_nodes > 0 ? P.smem_nodes * 64 : 0;
     int grid = 0;

@@ -172,8 +172,10 @@ struct TraceCtx {
 // One node visit of segment i: test both child boxes, test the triangles of
 // child leaves, then descend (near child first, far child pushed) or pop.
 // Returns true when the segment is finished (stack empty, a BOOL crossing,
-// a stack overflow, or the visit bound).
-template <int MODE, int STACK, bool STATS>
+// a stack overflow, or the visit bound).  TL: the tree has a top treelet
+// (negative node ids, children flagged by a negative count); without one
+// every node is a global slot and those tests are compiled out.
+template <int MODE, int STACK, bool STATS, bool TL>
 __device__ __forceinline__ bool node_step(const TraceCtx& C, const Seg& s, int64_t i, int& node,
                                           int& sp, int* stack, float& tlim, Result& res,
                                           int& visits, bool& overflow, TravStats& st) {
@@ -183,7 +185,7 @@ __device__ __forceinline__ bool node_step(const TraceCtx& C, const Seg& s, int64
     }
     ulonglong2 q0, q1, q2;
     int4 rc;
-    if (node < 0) {
+    if (TL && node < 0) {
         const int k = ~node;
         if (k < C.S) {
             const ulonglong2* p = (const ulonglong2*)(C.snodes + 4 * k);
@@ -216,7 +218,7 @@ __device__ __forceinline__ bool node_step(const TraceCtx& C, const Seg& s, int64
             return true;
     }
     const bool g0 = h0 && c0 <= 0, g1 = h1 && c1 <= 0;
-    const int x0 = c0 < 0 ? ~r0 : r0, x1 = c1 < 0 ? ~r1 : r1;
+    const int x0 = TL && c0 < 0 ? ~r0 : r0, x1 = TL && c1 < 0 ? ~r1 : r1;
     if (g0 && g1) {
         if (sp >= STACK) {
             overflow = true;
@@ -309,29 +311,31 @@ __device__ __forceinline__ bool node_step4(const TraceCtx& C, const Seg& s, int6
     return false;
 }
 
-// Whole traversal of one segment (used for the deep-stack re-run).
-// Returns false when the stack overflowed (result incomplete).
-template <int MODE, int STACK, bool STATS>
-__device__ __forceinline__ bool trace(const TraceCtx& C, const Seg& s, int64_t i, Result& res,
-                                      TravStats& st) {
+// Whole traversal of one segment from `root` (used for the deep-stack
+// re-run).  Returns false when the stack overflowed (result incomplete).
+template <int MODE, int STACK, bool STATS, bool TL>
+__device__ __forceinline__ bool trace(const TraceCtx& C, const Seg& s, int64_t i, int root,
+                                      Result& res, TravStats& st) {
     int stack[STACK];
-    int sp = 0, node = C.root, visits = 0;
+    int sp = 0, node = root, visits = 0;
     float tlim = 1.f;
     bool overflow = false;
-    while (!node_step<MODE, STACK, STATS>(C, s, i, node, sp, stack, tlim, res, visits, overflow, st)) {
+    while (!node_step<MODE, STACK, STATS, TL>(C, s, i, node, sp, stack, tlim, res, visits, overflow,
+                                              st)) {
     }
     return !overflow;
 }
 
 // Deep-stack re-run for segments whose stack overflowed (a radix tree over
-// 62-bit keys is at most 63 levels deep, so 64 entries always suffice).
-template <int MODE, bool STATS>
-__device__ __noinline__ void trace_deep(const TraceCtx& C, const Seg& s, int64_t i, Result& res,
-                                        TravStats& st) {
+// 62-bit keys is at most 63 levels deep, so 64 entries always suffice), on
+// binary nodes from `root`: the treelet root ~0 needs TL, a global slot not.
+template <int MODE, bool STATS, bool TL>
+__device__ __noinline__ void trace_deep(const TraceCtx& C, const Seg& s, int64_t i, int root,
+                                        Result& res, TravStats& st) {
     res.count = 0;
     res.best = -1;
     res.b64 = false;
-    trace<MODE, 64, STATS>(C, s, i, res, st);
+    trace<MODE, 64, STATS, TL>(C, s, i, root, res, st);
 }
 
 __device__ __forceinline__ void result_init(Result& r) {
@@ -506,7 +510,7 @@ __device__ __forceinline__ bool wait_flag(const int32_t* flag, int32_t* status, 
 // ordering of the segments); outputs still go to the segment's own index.
 // Dense outputs are written as segments finish; compaction is
 // warp-aggregated.  Must be called by all 32 lanes of the warp.
-template <int MODE, int STACK, bool STATS, int W>
+template <int MODE, int STACK, bool STATS, int W, bool TL>
 __device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long* counter,
                                            int64_t lo, int64_t hi, TravStats& st,
                                            unsigned long long& segs) {
@@ -585,11 +589,13 @@ __device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long
                 done = node_step4<MODE, STACK, STATS>(C, s, i, node, sp, stack, tlim, res, visits,
                                                       overflow, st);
             else
-                done = node_step<MODE, STACK, STATS>(C, s, i, node, sp, stack, tlim, res, visits,
+                done = node_step<MODE, STACK, STATS, TL>(C, s, i, node, sp, stack, tlim, res, visits,
                                                      overflow, st);
             if (done && (STACK < 64 || W == 4) && overflow) {
                 if (STATS) ++st.overflows;
-                trace_deep<MODE, STATS>(C, s, i, res, st);
+                // 4-wide traversal re-runs on binary nodes from the global root
+                trace_deep<MODE, STATS, TL && W != 4>(C, s, i, W == 4 ? C.root4 : C.root, res,
+                                                      st);
             }
         }
     }
