@@ -259,9 +259,9 @@ def run_ours(args):
         fp32_tflops = rsi.fp32_peak(1 << 20, stream=stream)
 
         # end to end through the public API from pinned host memory: the
-        # build plus rsi_intersect_host every step (the kernel reads the
-        # pinned segments in place over the CPU-GPU link, the flags come back
-        # with one device-to-host copy)
+        # build plus rsi_intersect_host every step (the copy engine streams
+        # the pinned segments into device staging under one persistent
+        # traversal; the flags come back with one device-to-host copy)
         hA = torch.from_numpy(seg.A).pin_memory()
         hB = torch.from_numpy(seg.B).pin_memory()
         hout = {"flag": torch.empty(n_seg, dtype=torch.uint8).pin_memory()}

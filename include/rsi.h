@@ -306,13 +306,17 @@ rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR
  * persistent traversal starts at once while the copy engine streams the
  * segments into device staging in chunks of `chunk` (0 -> 2^19, rounded up
  * to 32) and flags each chunk as it lands, the warps waiting (bounded:
- * RSI_ERR_TIMEOUT in the handle's status) for the chunks they take (25 B
- * per segment of staging); in COUNT / NEAREST the traversal kernel reads
- * the segments in place over the CPU-GPU link.  Otherwise each chunk is
- * first copied to the staging buffer, overlapped with the previous chunk's
- * traversal.  The work is ordered after everything already on s,
- * and s waits for it: the host outputs are complete once s is synchronised
- * (hA and hB must stay unchanged until then).  Pageable host memory is
+ * RSI_ERR_TIMEOUT in the handle's status) for the chunks they take (two
+ * staging slots used in turn, 25 B per segment each); in COUNT / NEAREST
+ * the traversal kernel reads the segments in place over the CPU-GPU link.
+ * Otherwise each chunk is first copied to the staging buffer, overlapped
+ * with the previous chunk's traversal.  The traversal is ordered after
+ * everything already on s, and s waits for the whole call: the host outputs
+ * are complete once s is synchronised (hA and hB must stay unchanged until
+ * then).  In the streamed BOOL path the copies of hA and hB wait only for
+ * their staging slot (the call before the previous one), not for s, so
+ * that they overlap the work already on s (a build, the previous call's
+ * traversal): hA and hB must hold their data when the call is made.  Pageable host memory is
  * staged by the driver and overlaps less.  Segments are processed in input
  * order (lo->sort_bits is ignored).  Errors as rsi_intersect, plus
  * RSI_ERR_OOM. */

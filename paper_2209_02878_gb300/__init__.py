@@ -255,7 +255,9 @@ class BVH:
         copy / launch chunk in segments (0: the library's choice).  Returns a
         dict of host output tensors (pinned when allocated here), complete
         once `stream` (default current) is synchronised; A and B must stay
-        unchanged until then."""
+        unchanged until then.  The streamed BOOL copies start without
+        waiting for `stream` (they overlap the work already queued there),
+        so pinned A and B must hold their data when this is called."""
         for t, nme in ((A, "A"), (B, "B")):
             if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32 or \
                     t.dim() != 2 or t.shape[1] != 3 or not t.is_contiguous():

@@ -178,10 +178,12 @@ struct rsi_bvh_s {
     char* pipe_mem = nullptr;
     size_t pipe_bytes = 0;
     int32_t* one = nullptr;  // pinned host 1: the value of a streamed chunk's ready flag
-    // streamed path: the staging is free again once this event (recorded
-    // after the previous streamed call's traversal and copy back) completes
-    cudaEvent_t sev_free = nullptr, sev_reset = nullptr;
-    bool sfree_valid = false;
+    // streamed path: two staging slots used in turn; slot q is free again
+    // once sev_free[q] (recorded after the traversal and copy back of the
+    // last streamed call that used it) completes
+    cudaEvent_t sev_free[2] = {nullptr, nullptr}, sev_reset = nullptr;
+    bool sfree_valid[2] = {false, false};
+    int sslot = 0;
     cudaStream_t pipe_stream = nullptr;
     // odd-parity workspace (rsi_points_inside): segment ends + counts
     char* in_mem = nullptr;
@@ -378,7 +380,8 @@ rsi_status rsi_bvh_destroy(rsi_bvh h) {
         if (h->pev_done[q]) cudaEventDestroy(h->pev_done[q]);
     }
     if (h->pev_start) cudaEventDestroy(h->pev_start);
-    if (h->sev_free) cudaEventDestroy(h->sev_free);
+    for (int q = 0; q < 2; ++q)
+        if (h->sev_free[q]) cudaEventDestroy(h->sev_free[q]);
     if (h->sev_reset) cudaEventDestroy(h->sev_reset);
     if (h->one) cudaFreeHost(h->one);
     cudaError_t e = rsi::dev_free(h->hooks, h->mem, h->stream);
@@ -566,11 +569,15 @@ static const float* mapped_host(const float* p, size_t bytes) {
 // internal stream and sets each chunk's ready flag by a 4-byte copy after
 // its data; a warp waits (bounded) for the flag of the chunk it takes
 // segments from.  The copy (~211 GB/s) and the traversal overlap instead of
-// one waiting for the other.  The copies wait only for the previous streamed
-// call to be done with the staging (not for everything on s), so they
-// overlap whatever precedes this call on s, e.g. the tree build; the flags
-// are reset on the copy stream and the traversal waits for that reset.
-// Staging: 24 B + 1 B per segment, held by the handle.
+// one waiting for the other.  Two staging slots are used in turn, and the
+// copies wait only until their slot is free (the call before the previous
+// one is done with it), not for everything on s: the copies of one call run
+// during the build and the traversal of the previous one, so back-to-back
+// calls keep the copy engine busy.  The flags are reset on the copy stream
+// and the traversal waits for that reset.  The traversal is queued before
+// the copies, so it starts as soon as s allows, however long the host takes
+// to queue the copies.  Staging: 2 x (24 B + 1 B) per segment, held by the
+// handle.
 static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB, int64_t nR,
                                      const rsi_output* hout, int64_t chunk,
                                      const rsi_launch_opts* lo, cudaStream_t cs) {
@@ -579,45 +586,64 @@ static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB
     ch = (ch + 31) / 32 * 32;
     const int64_t nc = (nR + ch - 1) / ch;
     const size_t ab = align256(12 * (size_t)nR), fb = align256((size_t)nR);
-    const size_t need = 2 * ab + fb + align256(4 * (size_t)nc);
-    if (!h->sev_free) {
-        RSI_CK(cudaEventCreateWithFlags(&h->sev_free, cudaEventDisableTiming));
+    const size_t slot_need = 2 * ab + fb + align256(4 * (size_t)nc);
+    if (!h->sev_reset) {
+        for (int q = 0; q < 2; ++q)
+            RSI_CK(cudaEventCreateWithFlags(&h->sev_free[q], cudaEventDisableTiming));
         RSI_CK(cudaEventCreateWithFlags(&h->sev_reset, cudaEventDisableTiming));
     }
-    bool fresh = false;  // staging (re)allocated on s: the copies must follow s
-    if (h->pipe_bytes < need) {
-        fresh = true;
+    if (h->pipe_bytes < 2 * slot_need) {  // (re)allocated on s: the copies must follow s
+        h->sfree_valid[0] = h->sfree_valid[1] = false;
         if (h->pipe_mem) {
             RSI_CK(rsi::dev_free(h->hooks, h->pipe_mem, h->pipe_stream));
             h->pipe_mem = nullptr;
             h->pipe_bytes = 0;
         }
-        cudaError_t e = rsi::dev_alloc(h->hooks, (void**)&h->pipe_mem, need, cs);
+        cudaError_t e = rsi::dev_alloc(h->hooks, (void**)&h->pipe_mem, 2 * slot_need, cs);
         if (e != cudaSuccess) {
             cudaGetLastError();
             h->pipe_mem = nullptr;
             return e == cudaErrorMemoryAllocation ? RSI_ERR_OOM : RSI_ERR_CUDA;
         }
-        h->pipe_bytes = need;
+        h->pipe_bytes = 2 * slot_need;
         h->pipe_stream = cs;
     }
     if (!h->one) {
         RSI_CK(cudaHostAlloc((void**)&h->one, sizeof(int32_t), cudaHostAllocDefault));
         *h->one = 1;
     }
-    float* dA = (float*)h->pipe_mem;
-    float* dB = (float*)(h->pipe_mem + ab);
-    uint8_t* dflag = (uint8_t*)(h->pipe_mem + 2 * ab);
-    int32_t* ready = (int32_t*)(h->pipe_mem + 2 * ab + fb);
+    // slot q at a fixed offset (half the allocation, whatever nR), so that
+    // it never overlaps the other slot that a running call may still read
+    const int q = h->sslot;
+    h->sslot ^= 1;
+    char* base = h->pipe_mem + q * (h->pipe_bytes / 512 * 256);
+    float* dA = (float*)base;
+    float* dB = (float*)(base + ab);
+    uint8_t* dflag = (uint8_t*)(base + 2 * ab);
+    int32_t* ready = (int32_t*)(base + 2 * ab + fb);
     cudaStream_t cp = h->pst[0];
-    if (fresh || !h->sfree_valid) {
+    if (!h->sfree_valid[q]) {
         RSI_CK(cudaEventRecord(h->pev_start, cs));
         RSI_CK(cudaStreamWaitEvent(cp, h->pev_start, 0));
     } else {
-        RSI_CK(cudaStreamWaitEvent(cp, h->sev_free, 0));
+        RSI_CK(cudaStreamWaitEvent(cp, h->sev_free[q], 0));
     }
     RSI_CK(cudaMemsetAsync(ready, 0, 4 * (size_t)nc, cp));
     RSI_CK(cudaEventRecord(h->sev_reset, cp));
+    rsi_output dout;
+    memset(&dout, 0, sizeof(dout));
+    dout.flag = dflag;
+    RSI_CK(cudaStreamWaitEvent(cs, h->sev_reset, 0));  // never a previous call's flags
+    h->sfree_valid[q] = false;
+    const rsi_status st = intersect_impl(h, dA, dB, nR, RSI_MODE_BOOL, &dout, lo, (rsi_stream)cs,
+                                         false, nullptr, ready, ch);
+    if (st == RSI_OK) {
+        RSI_CK(cudaMemcpyAsync(hout->flag, dflag, (size_t)nR, cudaMemcpyDeviceToHost, cs));
+        RSI_CK(cudaEventRecord(h->sev_free[q], cs));
+        h->sfree_valid[q] = true;
+    }
+    // the copies are queued even when the launch failed: a traversal that
+    // did start always finds its chunks' flags set
     for (int64_t c = 0; c < nc; ++c) {
         const int64_t off = c * ch, n = nR - off < ch ? nR - off : ch;
         RSI_CK(cudaMemcpyAsync(dA + 3 * off, hA + 3 * off, 12 * (size_t)n, cudaMemcpyHostToDevice,
@@ -626,20 +652,9 @@ static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB
                                cp));
         RSI_CK(cudaMemcpyAsync(ready + c, h->one, sizeof(int32_t), cudaMemcpyHostToDevice, cp));
     }
-    rsi_output dout;
-    memset(&dout, 0, sizeof(dout));
-    dout.flag = dflag;
-    RSI_CK(cudaStreamWaitEvent(cs, h->sev_reset, 0));  // never the previous call's flags
-    h->sfree_valid = false;
-    const rsi_status st = intersect_impl(h, dA, dB, nR, RSI_MODE_BOOL, &dout, lo, (rsi_stream)cs,
-                                         false, nullptr, ready, ch);
-    if (st != RSI_OK) return st;
-    RSI_CK(cudaMemcpyAsync(hout->flag, dflag, (size_t)nR, cudaMemcpyDeviceToHost, cs));
-    RSI_CK(cudaEventRecord(h->sev_free, cs));
-    h->sfree_valid = true;
     RSI_CK(cudaEventRecord(h->pev_done[0], cp));
     RSI_CK(cudaStreamWaitEvent(cs, h->pev_done[0], 0));
-    return RSI_OK;
+    return st;
 }
 
 rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64_t nR,
@@ -660,8 +675,8 @@ rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64
     lo2.sort_bits = -1;  // the segment-order workspace is shared: keep input order
     lo2.stats = 0;
     // Page-locked inputs: BOOL streams them into device staging while one
-    // persistent traversal runs (intersect_streamed: 1.49 ms for 10M
-    // segments on GB300); COUNT and NEAREST, whose larger outputs come back
+    // persistent traversal runs (intersect_streamed: 1.30 ms per call for
+    // 10M segments on GB300, back to back); COUNT and NEAREST, whose larger outputs come back
     // per chunk, read them in place over the CPU-GPU link (1.61 ms for BOOL,
     // against 1.74 ms for staging chunk by chunk; copies and in-place reads
     // running together compete for the same link).  Other host memory is
@@ -688,7 +703,8 @@ rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64
         lo2.packet = 0;  // the packet kernel does not wait for streamed chunks
         return intersect_streamed(h, hA, hB, nR, hout, chunk, &lo2, cs);
     }
-    h->sfree_valid = false;  // this call uses the staging too: a later streamed call follows s
+    // this call uses the staging too: a later streamed call follows s
+    h->sfree_valid[0] = h->sfree_valid[1] = false;
     // staging of buffer q: [A | B when copied] | outputs (flag / count /
     // tri, tuv, point, dist), each part 256-byte aligned
     const size_t in_b = in_place ? 0 : align256(12 * (size_t)ch);

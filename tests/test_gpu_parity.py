@@ -299,13 +299,16 @@ def test_points_inside_star_shaped_sphere():
     assert 0.2 < got.mean() < 0.8
 
 
-def test_stack_overflow_reruns_with_deep_stack():
+@pytest.mark.parametrize("levels", [0, 10])
+def test_stack_overflow_reruns_with_deep_stack(levels):
     """An 8-entry stack overflows on a deep tree; the overflowed segments are
-    re-run with the 64-entry stack and the results do not change."""
+    re-run with the 64-entry stack and the results do not change.  With a
+    top treelet (levels > 0) binary traversal re-runs from the treelet root
+    and 4-wide traversal from the global root."""
     rng = np.random.default_rng(12)
     mesh = synth.icosphere(7, rng)                 # 327,680 triangles
     seg = synth.segments_box(rng, 20000, [-1.5] * 3, [1.5] * 3, [-1.5] * 3, [1.5] * 3)
-    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T))
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T), top_levels=levels)
     A, B = dev(seg.A), dev(seg.B)
     deep = {m: bvh.intersect(A, B, m) for m in ("count", "nearest")}
     for w in (2, 4):
@@ -395,4 +398,29 @@ def test_host_calls_back_to_back(small):
         sel = slice(None) if n is None else slice(0, n)
         key = {"bool": "flag", "count": "count", "nearest": "tri"}[mode]
         np.testing.assert_array_equal(o[key].numpy(), ref[key][sel], err_msg=f"{mode} n={n}")
+    assert bvh.status() == 0
+
+
+def test_streamed_calls_alternate_staging_slots(small):
+    """Streamed BOOL calls only, back to back on one stream with different
+    segments, sizes and chunks and a rebuild now and then: consecutive calls
+    use the two staging slots in turn and a call's copies overlap the
+    previous call's traversal; every result matches the oracle's flags."""
+    mesh, seg, ref = small
+    V, T = dev(mesh.V), dev(mesh.T)
+    bvh = rsi.BVH(V, T)
+    rng = np.random.default_rng(5)
+    s = torch.cuda.Stream()
+    calls = []
+    for k, (n, chunk) in enumerate([(10000, 0), (6007, 1024), (9000, 64), (33, 0), (10000, 512),
+                                    (1, 0), (7777, 2048), (4096, 32), (10000, 0)]):
+        idx = rng.permutation(seg.n)[:n]
+        A = torch.from_numpy(seg.A[idx]).pin_memory()
+        B = torch.from_numpy(seg.B[idx]).pin_memory()
+        if k % 3 == 2:
+            bvh.build(V, T, stream=s)
+        calls.append((idx, bvh.intersect_host(A, B, "bool", chunk=chunk, stream=s), A, B))
+    s.synchronize()
+    for idx, o, _, _ in calls:
+        np.testing.assert_array_equal(o["flag"].numpy(), ref["flag"][idx], err_msg=f"n={idx.size}")
     assert bvh.status() == 0
