@@ -39,7 +39,7 @@ BYTES_PER_SEG_COUNT = 28
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_trace<BOOL> launch on
 # this workload (ncu, profiles/k_trace_bool_paper_scale.md), valid while the
 # traversal sources hash to `sha`; otherwise reported as null
-TRAFFIC = {"sha": "bbca41b9dc292f0c", "bytes": 259_491_840, "warp_inst": 995_817_467}
+TRAFFIC = {"sha": "13251166776d4519", "bytes": 258_686_208, "warp_inst": 961_160_469}
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle at
 # the maximum SM clock (2,070 MHz)
 ISSUE_PEAK = 152 * 4 * 2.070e9

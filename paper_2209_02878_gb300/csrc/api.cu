@@ -574,10 +574,11 @@ static const float* mapped_host(const float* p, size_t bytes) {
 // one is done with it), not for everything on s: the copies of one call run
 // during the build and the traversal of the previous one, so back-to-back
 // calls keep the copy engine busy.  The flags are reset on the copy stream
-// and the traversal waits for that reset.  The traversal is queued before
-// the copies, so it starts as soon as s allows, however long the host takes
-// to queue the copies.  Staging: 2 x (24 B + 1 B) per segment, held by the
-// handle.
+// and the traversal waits for that reset.  The copies are queued before the
+// traversal: where a launch blocks the host until the kernel ends
+// (CUDA_LAUNCH_BLOCKING, a profiler's replay), a traversal queued first
+// would wait for copies not yet queued until its bounded waits ran out.
+// Staging: 2 x (24 B + 1 B) per segment, held by the handle.
 static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB, int64_t nR,
                                      const rsi_output* hout, int64_t chunk,
                                      const rsi_launch_opts* lo, cudaStream_t cs) {
@@ -630,20 +631,7 @@ static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB
     }
     RSI_CK(cudaMemsetAsync(ready, 0, 4 * (size_t)nc, cp));
     RSI_CK(cudaEventRecord(h->sev_reset, cp));
-    rsi_output dout;
-    memset(&dout, 0, sizeof(dout));
-    dout.flag = dflag;
-    RSI_CK(cudaStreamWaitEvent(cs, h->sev_reset, 0));  // never a previous call's flags
     h->sfree_valid[q] = false;
-    const rsi_status st = intersect_impl(h, dA, dB, nR, RSI_MODE_BOOL, &dout, lo, (rsi_stream)cs,
-                                         false, nullptr, ready, ch);
-    if (st == RSI_OK) {
-        RSI_CK(cudaMemcpyAsync(hout->flag, dflag, (size_t)nR, cudaMemcpyDeviceToHost, cs));
-        RSI_CK(cudaEventRecord(h->sev_free[q], cs));
-        h->sfree_valid[q] = true;
-    }
-    // the copies are queued even when the launch failed: a traversal that
-    // did start always finds its chunks' flags set
     for (int64_t c = 0; c < nc; ++c) {
         const int64_t off = c * ch, n = nR - off < ch ? nR - off : ch;
         RSI_CK(cudaMemcpyAsync(dA + 3 * off, hA + 3 * off, 12 * (size_t)n, cudaMemcpyHostToDevice,
@@ -653,8 +641,21 @@ static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB
         RSI_CK(cudaMemcpyAsync(ready + c, h->one, sizeof(int32_t), cudaMemcpyHostToDevice, cp));
     }
     RSI_CK(cudaEventRecord(h->pev_done[0], cp));
+    rsi_output dout;
+    memset(&dout, 0, sizeof(dout));
+    dout.flag = dflag;
+    RSI_CK(cudaStreamWaitEvent(cs, h->sev_reset, 0));  // never a previous call's flags
+    const rsi_status st = intersect_impl(h, dA, dB, nR, RSI_MODE_BOOL, &dout, lo, (rsi_stream)cs,
+                                         false, nullptr, ready, ch);
+    if (st != RSI_OK) {
+        cudaStreamWaitEvent(cs, h->pev_done[0], 0);  // hA, hB are read until then
+        return st;
+    }
+    RSI_CK(cudaMemcpyAsync(hout->flag, dflag, (size_t)nR, cudaMemcpyDeviceToHost, cs));
+    RSI_CK(cudaEventRecord(h->sev_free[q], cs));
+    h->sfree_valid[q] = true;
     RSI_CK(cudaStreamWaitEvent(cs, h->pev_done[0], 0));
-    return st;
+    return RSI_OK;
 }
 
 rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64_t nR,

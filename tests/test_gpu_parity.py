@@ -424,3 +424,36 @@ def test_streamed_calls_alternate_staging_slots(small):
     for idx, o, _, _ in calls:
         np.testing.assert_array_equal(o["flag"].numpy(), ref["flag"][idx], err_msg=f"n={idx.size}")
     assert bvh.status() == 0
+
+
+_BLOCKING_CHILD = r"""
+import numpy as np, torch
+import paper_2209_02878_gb300 as rsi
+from paper_2209_02878_gb300 import synth
+mesh, seg = synth.workload_small_bool()
+V, T = torch.from_numpy(mesh.V).cuda(), torch.from_numpy(mesh.T).cuda()
+A, B = torch.from_numpy(seg.A).pin_memory(), torch.from_numpy(seg.B).pin_memory()
+bvh = rsi.BVH(V, T)
+want = bvh.intersect(A.cuda(), B.cuda(), "bool")["flag"].cpu()
+outs = [bvh.intersect_host(A, B, "bool", chunk=1024) for _ in range(3)]
+torch.cuda.synchronize()
+assert all(torch.equal(o["flag"], want) for o in outs)
+assert bvh.status() == 0, bvh.status()
+print("ok")
+"""
+
+
+def test_streamed_call_with_blocking_launches():
+    """With CUDA_LAUNCH_BLOCKING=1 a launch returns only when its kernel has
+    ended, so the streamed path must queue the chunk copies before the
+    traversal that waits for them: the calls finish with correct flags and
+    no timeout in the status."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_LAUNCH_BLOCKING="1",
+               PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    r = subprocess.run([sys.executable, "-c", _BLOCKING_CHILD], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
