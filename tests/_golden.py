@@ -1,0 +1,39 @@
+"""Reader of the text fixtures under tests/golden/ (hand-derived expected
+values; each file states its derivation and the passage it follows)."""
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _vecs(text, dtype):
+    return np.array([[float(x) for x in v.split(",")] for v in text.split()], dtype)
+
+
+def load_mt_cases(name="mt_hand_cases.txt"):
+    """One dict per case: name, V float32 [nV,3], T int32 [nT,3], A, B
+    float32 [1,3], flag, count, tri, and for hits tuv, point, dist."""
+    cases = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            fields = [f.strip() for f in line.split(";")]
+            c = {"name": fields[0]}
+            for f in fields[1:]:
+                key, val = f.split("=", 1)
+                c[key] = val
+            case = {"name": c["name"],
+                    "V": _vecs(c["V"], np.float32),
+                    "T": _vecs(c["T"], np.float64).astype(np.int32),
+                    "A": _vecs(c["a"], np.float32),
+                    "B": _vecs(c["b"], np.float32),
+                    "flag": int(c["flag"]), "count": int(c["count"]), "tri": int(c["tri"])}
+            if "tuv" in c:
+                case["tuv"] = np.array([float(x) for x in c["tuv"].split(",")])
+                case["point"] = np.array([float(x) for x in c["point"].split(",")])
+                case["dist"] = float(c["dist"])
+            cases.append(case)
+    return cases

@@ -8,6 +8,8 @@ import pytest
 
 from paper_2209_02878_gb300 import synth
 
+from _golden import load_mt_cases
+
 UNIT = ([0, 0, 0], [1, 0, 0], [0, 1, 0])
 
 
@@ -24,6 +26,20 @@ def test_axis_aligned_hit_exact(orc):
     assert tuple(o["point"][0]) == (0.25, 0.25, 0.0)
     assert o["dist"][0] == 1.0
     assert o["neardeg"][0] == 0
+
+
+@pytest.mark.parametrize("case", load_mt_cases(), ids=lambda c: c["name"])
+def test_golden_hand_cases(orc, case):
+    """tests/golden/mt_hand_cases.txt: hand-derived flags, counts, nearest
+    triangles and exact (t, u, v), points and distances (dyadic inputs, so
+    FP64 reproduces them exactly)."""
+    o = orc.brute(case["V"], case["T"], case["A"], case["B"])
+    assert (o["flag"][0], o["count"][0], o["tri"][0]) == \
+        (case["flag"], case["count"], case["tri"]), case["name"]
+    if "tuv" in case:
+        assert list(o["tuv"][0]) == list(case["tuv"]), case["name"]
+        assert list(o["point"][0]) == list(case["point"]), case["name"]
+        assert o["dist"][0] == case["dist"], case["name"]
 
 
 @pytest.mark.parametrize("a,b,why", [
