@@ -37,3 +37,24 @@ def load_mt_cases(name="mt_hand_cases.txt"):
                 case["dist"] = float(c["dist"])
             cases.append(case)
     return cases
+
+
+def load_backward_cases(name="backward_hand_cases.txt"):
+    """One dict per case: name, V, T, A, B as for load_mt_cases, gP and gtuv
+    float64 [1,3], and the expected gA, gB [1,3] and gV [nV,3]."""
+    cases = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            fields = [f.strip() for f in line.split(";")]
+            c = dict(f.split("=", 1) for f in fields[1:])
+            cases.append({"name": fields[0],
+                          "V": _vecs(c["V"], np.float32),
+                          "T": _vecs(c["T"], np.float64).astype(np.int32),
+                          "A": _vecs(c["a"], np.float32), "B": _vecs(c["b"], np.float32),
+                          "gP": _vecs(c["gP"], np.float64), "gtuv": _vecs(c["gtuv"], np.float64),
+                          "gA": _vecs(c["gA"], np.float64), "gB": _vecs(c["gB"], np.float64),
+                          "gV": _vecs(c["gV"], np.float64)})
+    return cases

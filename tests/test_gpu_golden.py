@@ -1,14 +1,14 @@
-"""GPU parity on the hand-derived cases of tests/golden/mt_hand_cases.txt:
-the CUDA path (through the C ABI binding), one small mesh per case.  Flags,
-counts and nearest triangles must match exactly; (t, u, v), points and
-distances within relative 1e-5 (the parity tolerance of the FP32 outputs)."""
+"""GPU parity on the hand-derived cases of tests/golden/: the CUDA path
+(through the C ABI binding), one small mesh per case.  Flags, counts and
+nearest triangles must match exactly; (t, u, v), points, distances and
+gradients within relative 1e-5 (the parity tolerance of the FP32 outputs)."""
 import numpy as np
 import pytest
 import torch
 
 import paper_2209_02878_gb300 as rsi
 
-from _golden import load_mt_cases
+from _golden import load_backward_cases, load_mt_cases
 from _util import assert_close
 
 pytestmark = pytest.mark.gpu
@@ -34,3 +34,16 @@ def test_golden_hand_cases(case):
         assert_close(n["dist"].cpu().numpy()[:1], [case["dist"]], what=case["name"] + " dist")
     assert bvh.status() == 0
     bvh.close()
+
+
+@pytest.mark.parametrize("case", load_backward_cases(), ids=lambda c: c["name"])
+def test_golden_backward_cases(case):
+    V, T, A, B = dev(case["V"]), dev(case["T"]), dev(case["A"]), dev(case["B"])
+    tri = torch.zeros(1, dtype=torch.int32, device=DEV)
+    gP = dev(case["gP"].astype(np.float32))
+    gtuv = dev(case["gtuv"].astype(np.float32))
+    gV, gA, gB = rsi.intersect_backward(V, T, A, B, tri, grad_point=gP, grad_tuv=gtuv)
+    torch.cuda.synchronize()
+    assert_close(gA.cpu().numpy(), case["gA"], what=case["name"] + " gA")
+    assert_close(gB.cpu().numpy(), case["gB"], what=case["name"] + " gB")
+    assert_close(gV.cpu().numpy(), case["gV"], what=case["name"] + " gV")

@@ -6,6 +6,8 @@ import pytest
 
 from paper_2209_02878_gb300 import synth
 
+from _golden import load_backward_cases
+
 
 def test_closed_form_unit_triangle(orc):
     # plane z=0 through v0=(0,0,0), v1=(1,0,0), v2=(0,1,0); vertical segment at
@@ -35,6 +37,18 @@ def test_closed_form_unit_triangle(orc):
     # moving a along x with b fixed moves P_x = u by (1-t) per unit
     assert np.isclose(gA[0, 0], 1 - t, rtol=1e-14)
     assert np.isclose(gB[0, 0], t, rtol=1e-14)
+
+
+@pytest.mark.parametrize("case", load_backward_cases(), ids=lambda c: c["name"])
+def test_golden_backward_cases(orc, case):
+    """tests/golden/backward_hand_cases.txt: every gradient component of a
+    combined loss on P and (t, u, v), derived by hand (dyadic, so FP64 holds
+    them to the last bit up to the rounding of its few divisions)."""
+    gV, gA, gB = orc.backward(case["V"], case["T"], case["A"], case["B"],
+                              np.array([0], np.int32), gP=case["gP"], gtuv=case["gtuv"])
+    np.testing.assert_allclose(gA, case["gA"], rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(gB, case["gB"], rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(gV, case["gV"], rtol=1e-14, atol=1e-14)
 
 
 def _problem(seed=0, G=33, n=4000):
