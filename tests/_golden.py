@@ -58,3 +58,29 @@ def load_backward_cases(name="backward_hand_cases.txt"):
                           "gA": _vecs(c["gA"], np.float64), "gB": _vecs(c["gB"], np.float64),
                           "gV": _vecs(c["gV"], np.float64)})
     return cases
+
+
+def load_lbvh_case(name="lbvh_hand_case.txt"):
+    """The hand-worked build: a point mesh (V, T: degenerate triangles whose
+    corners coincide, so each centroid is its point) and the expected
+    bounds, per-triangle codes, order, left / right children, ranges and
+    three internal boxes."""
+    c = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                c[k] = v
+    P = _vecs(c["points"], np.float32)
+    out = {"V": np.repeat(P, 3, axis=0),
+           "T": np.arange(3 * len(P), dtype=np.int32).reshape(-1, 3),
+           "bounds": [float(x) for x in c["bounds"].split(",")],
+           "codes": [int(x) for x in c["codes"].split()],
+           "order": [int(x) for x in c["order"].split()],
+           "left": [int(x) for x in c["left"].split()],
+           "right": [int(x) for x in c["right"].split()],
+           "range": [[int(x) for x in r.split(",")] for r in c["range"].split()]}
+    for k in ("nbox0", "nbox3", "nbox4"):
+        out[k] = [float(x) for x in c[k].split(",")]
+    return out

@@ -8,7 +8,7 @@ import torch
 
 import paper_2209_02878_gb300 as rsi
 
-from _golden import load_backward_cases, load_mt_cases
+from _golden import load_backward_cases, load_lbvh_case, load_mt_cases
 from _util import assert_close
 
 pytestmark = pytest.mark.gpu
@@ -47,3 +47,21 @@ def test_golden_backward_cases(case):
     assert_close(gA.cpu().numpy(), case["gA"], what=case["name"] + " gA")
     assert_close(gB.cpu().numpy(), case["gB"], what=case["name"] + " gB")
     assert_close(gV.cpu().numpy(), case["gV"], what=case["name"] + " gV")
+
+
+def test_golden_lbvh_build():
+    """The hand-worked build of tests/golden/lbvh_hand_case.txt on the
+    device: bounds, codes (exported in sorted order), order, children,
+    ranges and internal boxes exactly."""
+    c = load_lbvh_case()
+    bvh = rsi.BVH(dev(c["V"]), dev(c["T"]))
+    g = bvh.export()
+    assert list(g["bounds"]) == c["bounds"]
+    assert list(g["order"]) == c["order"]
+    assert list(g["codes"]) == [c["codes"][i] for i in c["order"]]
+    assert list(g["left"]) == c["left"]
+    assert list(g["right"]) == c["right"]
+    assert g["range"].tolist() == c["range"]
+    for k in (0, 3, 4):
+        assert g["nbox"][k].tolist() == c[f"nbox{k}"]
+    bvh.close()

@@ -8,7 +8,7 @@ import pytest
 
 from paper_2209_02878_gb300 import synth
 
-from _golden import load_mt_cases
+from _golden import load_lbvh_case, load_mt_cases
 
 UNIT = ([0, 0, 0], [1, 0, 0], [0, 1, 0])
 
@@ -302,23 +302,19 @@ def _point_mesh(points):
 
 
 def test_lbvh_hand_example(orc):
-    # centroids at exact binary fractions so q and the codes are exact:
-    # c0=(0,0,0)->0, c1=(1,1,1)->2^30-1, c2=(.5,0,0)->2^29, c3=(0,.5,0)->2^28,
-    # c4=(.25,0,0)->2^26, c5=(0,0,0)->0.  Sorted: [0,5,4,3,2,1];
-    # K_i = code<<32|i; root [0,5] splits after leaf 3 (K3 is the last key with
-    # more than 2 leading bits in common with K0), [0,3] after 2, [0,2] after 1.
-    V, T = _point_mesh([[0, 0, 0], [1, 1, 1], [.5, 0, 0], [0, .5, 0], [.25, 0, 0], [0, 0, 0]])
-    o = orc.lbvh(V, T)
-    assert list(o["bounds"]) == [0, 0, 0, 1, 1, 1]
-    assert list(o["codes"]) == [0, (1 << 30) - 1, 1 << 29, 1 << 28, 1 << 26, 0]
-    assert list(o["order"]) == [0, 5, 4, 3, 2, 1]
-    assert list(o["left"]) == [3, -1, 1, 2, -5]
-    assert list(o["right"]) == [4, -2, -3, -4, -6]
-    assert o["range"].tolist() == [[0, 5], [0, 1], [0, 2], [0, 3], [4, 5]]
-    assert o["nbox"][0].tolist() == [0, 0, 0, 1, 1, 1]
-    # node 3 holds triangles 0,5,4,3 at (0,0,0),(0,0,0),(.25,0,0),(0,.5,0)
-    assert o["nbox"][3].tolist() == [0, 0, 0, 0.25, 0.5, 0]
-    assert o["nbox"][4].tolist() == [0.5, 0, 0, 1, 1, 1]      # leaves 2,1
+    """tests/golden/lbvh_hand_case.txt: six centroids at binary fractions, so
+    the quantised coordinates, codes, order, radix tree and boxes are exact
+    (derivation in the file)."""
+    c = load_lbvh_case()
+    o = orc.lbvh(c["V"], c["T"])
+    assert list(o["bounds"]) == c["bounds"]
+    assert list(o["codes"]) == c["codes"]
+    assert list(o["order"]) == c["order"]
+    assert list(o["left"]) == c["left"]
+    assert list(o["right"]) == c["right"]
+    assert o["range"].tolist() == c["range"]
+    for k in (0, 3, 4):
+        assert o["nbox"][k].tolist() == c[f"nbox{k}"]
 
 
 def _trie_tree(keys):
