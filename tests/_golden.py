@@ -84,3 +84,19 @@ def load_lbvh_case(name="lbvh_hand_case.txt"):
     for k in ("nbox0", "nbox3", "nbox4"):
         out[k] = [float(x) for x in c[k].split(",")]
     return out
+
+
+def load_inside_case(name="cube_inside_cases.txt"):
+    """The closed cube: V float32 [8,3], T int32 [12,3], points P float32
+    [n,3] and the expected inside flags uint8 [n]."""
+    c = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                c[k] = v
+    return {"V": _vecs(c["V"], np.float32),
+            "T": _vecs(c["T"], np.float64).astype(np.int32),
+            "P": _vecs(c["P"], np.float32),
+            "inside": np.array([int(x) for x in c["inside"].split()], np.uint8)}

@@ -8,7 +8,7 @@ import torch
 
 import paper_2209_02878_gb300 as rsi
 
-from _golden import load_backward_cases, load_lbvh_case, load_mt_cases
+from _golden import load_backward_cases, load_inside_case, load_lbvh_case, load_mt_cases
 from _util import assert_close
 
 pytestmark = pytest.mark.gpu
@@ -64,4 +64,14 @@ def test_golden_lbvh_build():
     assert g["range"].tolist() == c["range"]
     for k in (0, 3, 4):
         assert g["nbox"][k].tolist() == c[f"nbox{k}"]
+    bvh.close()
+
+
+def test_golden_cube_inside():
+    """rsi_points_inside on the closed cube of tests/golden/cube_inside_cases.txt."""
+    c = load_inside_case()
+    bvh = rsi.BVH(dev(c["V"]), dev(c["T"]))
+    got = bvh.points_inside(dev(c["P"]))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(got.cpu().numpy(), c["inside"])
     bvh.close()

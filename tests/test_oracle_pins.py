@@ -8,7 +8,7 @@ import pytest
 
 from paper_2209_02878_gb300 import synth
 
-from _golden import load_lbvh_case, load_mt_cases
+from _golden import load_inside_case, load_lbvh_case, load_mt_cases
 
 UNIT = ([0, 0, 0], [1, 0, 0], [0, 1, 0])
 
@@ -390,3 +390,14 @@ def test_lbvh_quantisation_against_float32_numpy(orc):
     np.testing.assert_array_equal(o["codes"], codes)
     np.testing.assert_array_equal(o["bounds"], np.r_[lo, hi])
     np.testing.assert_array_equal(o["order"], np.lexsort((np.arange(len(codes)), codes)))
+
+
+def test_golden_cube_parity(orc):
+    """tests/golden/cube_inside_cases.txt: the crossing count of a segment
+    from each point along (0.31, 0.57, 0.76), 10 long, is odd exactly for
+    the points inside the closed cube."""
+    c = load_inside_case()
+    u = np.array([0.31, 0.57, 0.76])
+    B = (c["P"] + 10.0 * u / np.linalg.norm(u)).astype(np.float32)
+    o = orc.brute(c["V"], c["T"], c["P"], B)
+    np.testing.assert_array_equal(o["count"] % 2, c["inside"])
