@@ -49,13 +49,16 @@ __global__ void __maxnreg__(128) k_batch(BatchParams P) {
         C.out = it.out;
         switch (it.mode) {
             case RSI_MODE_BOOL:
-                trace_loop<RSI_MODE_BOOL, STACK, false, 2, false>(C, nullptr, tile.lo, tile.hi, st, segs);
+                trace_loop<RSI_MODE_BOOL, STACK, false, 2, false>(C, nullptr, tile.lo, tile.hi, st,
+                                                                  segs);
                 break;
             case RSI_MODE_COUNT:
-                trace_loop<RSI_MODE_COUNT, STACK, false, 2, false>(C, nullptr, tile.lo, tile.hi, st, segs);
+                trace_loop<RSI_MODE_COUNT, STACK, false, 2, false>(C, nullptr, tile.lo, tile.hi, st,
+                                                                   segs);
                 break;
             default:
-                trace_loop<RSI_MODE_NEAREST, STACK, false, 2, false>(C, nullptr, tile.lo, tile.hi, st, segs);
+                trace_loop<RSI_MODE_NEAREST, STACK, false, 2, false>(C, nullptr, tile.lo, tile.hi, st,
+                                                                     segs);
                 break;
         }
     }
