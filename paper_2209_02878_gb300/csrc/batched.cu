@@ -57,8 +57,8 @@ __global__ void __maxnreg__(128) k_batch(BatchParams P) {
                                                                    segs);
                 break;
             default:
-                trace_loop<RSI_MODE_NEAREST, STACK, false, 2, false>(C, nullptr, tile.lo, tile.hi, st,
-                                                                     segs);
+                trace_loop<RSI_MODE_NEAREST, STACK, false, 2, false>(C, nullptr, tile.lo, tile.hi,
+                                                                     st, segs);
                 break;
         }
     }
