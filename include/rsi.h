@@ -316,10 +316,10 @@ rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR
  * then).  In the streamed BOOL path the copies of hA and hB wait only for
  * their staging slot (the call before the previous one), not for s, so
  * that they overlap the work already on s (a build, the previous call's
- * traversal): hA and hB must hold their data when the call is made.  Pageable host memory is
- * staged by the driver and overlaps less.  Segments are processed in input
- * order (lo->sort_bits is ignored).  Errors as rsi_intersect, plus
- * RSI_ERR_OOM. */
+ * traversal): hA and hB must hold their data when the call is made.
+ * Pageable host memory is staged by the driver and overlaps less.  Segments
+ * are processed in input order (lo->sort_bits is ignored).  Errors as
+ * rsi_intersect, plus RSI_ERR_OOM. */
 rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64_t nR,
                               rsi_mode mode, const rsi_output* hout, int64_t chunk,
                               const rsi_launch_opts* lo, rsi_stream s);
