@@ -41,34 +41,38 @@ def compile_oracle(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _bind(lib):
+    """Set the ctypes prototypes of the oracle's entry points on `lib`."""
+    P = C.c_void_p
+    L = C.c_long
+    lib.orc_brute.argtypes = [P, L, P, L, P, P, L, C.c_int] + [P] * 7
+    lib.orc_brute.restype = C.c_int
+    lib.orc_bvh_build.argtypes = [P, L, P, L, C.c_double]
+    lib.orc_bvh_build.restype = P
+    lib.orc_bvh_free.argtypes = [P]
+    lib.orc_bvh_nodes.argtypes = [P]
+    lib.orc_bvh_nodes.restype = L
+    lib.orc_bvh_query.argtypes = [P, P, L, P, P, P, L, C.c_int] + [P] * 7
+    lib.orc_bvh_query.restype = C.c_int
+    lib.orc_backward.argtypes = [P, L, P, L, P, P, L, P, P, P, P, P, P]
+    lib.orc_backward.restype = C.c_int
+    lib.orc_eval_fixed.argtypes = [P, L, P, P, P, L, P, P]
+    lib.orc_eval_fixed.restype = C.c_int
+    lib.orc_lbvh.argtypes = [P, L, P, L] + [P] * 8
+    lib.orc_lbvh.restype = C.c_int
+    lib.orc_mt.argtypes = [P] * 6
+    lib.orc_morton3.argtypes = [C.c_uint32] * 3
+    lib.orc_morton3.restype = C.c_uint32
+    lib.orc_num_threads.restype = C.c_int
+    return lib
+
+
 def _get():
     global _lib
     with _lock:
         if _lib is None:
             compile_oracle()
-            lib = C.CDLL(_LIB_PATH)
-            P = C.c_void_p
-            L = C.c_long
-            lib.orc_brute.argtypes = [P, L, P, L, P, P, L, C.c_int] + [P] * 7
-            lib.orc_brute.restype = C.c_int
-            lib.orc_bvh_build.argtypes = [P, L, P, L, C.c_double]
-            lib.orc_bvh_build.restype = P
-            lib.orc_bvh_free.argtypes = [P]
-            lib.orc_bvh_nodes.argtypes = [P]
-            lib.orc_bvh_nodes.restype = L
-            lib.orc_bvh_query.argtypes = [P, P, L, P, P, P, L, C.c_int] + [P] * 7
-            lib.orc_bvh_query.restype = C.c_int
-            lib.orc_backward.argtypes = [P, L, P, L, P, P, L, P, P, P, P, P, P]
-            lib.orc_backward.restype = C.c_int
-            lib.orc_eval_fixed.argtypes = [P, L, P, P, P, L, P, P]
-            lib.orc_eval_fixed.restype = C.c_int
-            lib.orc_lbvh.argtypes = [P, L, P, L] + [P] * 8
-            lib.orc_lbvh.restype = C.c_int
-            lib.orc_mt.argtypes = [P] * 6
-            lib.orc_morton3.argtypes = [C.c_uint32] * 3
-            lib.orc_morton3.restype = C.c_uint32
-            lib.orc_num_threads.restype = C.c_int
-            _lib = lib
+            _lib = _bind(C.CDLL(_LIB_PATH))
     return _lib
 
 
