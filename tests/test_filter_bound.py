@@ -173,7 +173,8 @@ def test_certified_decisions_match_the_definition(seed):
     # the filter must decide most cases and leave the hardest to FP64
     assert 0.5 < cert.mean() < 1.0
     wrong = cert & ((res == 1) != hit)
-    assert not wrong.any(), f"{int(wrong.sum())} certified decisions differ, first {np.argmax(wrong)}"
+    assert not wrong.any(), \
+        f"{int(wrong.sum())} certified decisions differ, first {np.argmax(wrong)}"
     h = res == 1
     with np.errstate(invalid="ignore"):
         for name, x, x64 in (("t", t, t64), ("u", u, u64), ("v", v, v64)):
