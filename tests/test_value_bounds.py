@@ -1,6 +1,7 @@
-"""CPU checks of how the nearest crossing's (t, u, v) are produced when the
-decision filter's own bound is too loose for the 1e-5 output tolerance
-(the nearest mode of Sec. 2.4, values of the Sec. 2 definition):
+"""CPU checks of the values the kernels produce beyond the decisions: the
+nearest crossing's (t, u, v) when the decision filter's own bound is too
+loose for the 1e-5 output tolerance (the nearest mode of Sec. 2.4, values of
+the Sec. 2 definition), and the adjoint's gradients:
 
 - the tighter per-triangle bound (componentwise magnitudes and gamma_10,
   `mt32_tight` in csrc/rsi_internal.cuh) must cover the FP32 values'
@@ -8,16 +9,21 @@ decision filter's own bound is too loose for the 1e-5 output tolerance
   is safe;
 - the double-float recomputation (`mt_df`: two-sum / two-product pairs,
   about 44 bits) must land within the tolerance wherever that bound can
-  keep the determinant away from zero.
+  keep the determinant away from zero;
+- the adjoint's double-float algebra (`k_backward` in csrc/backward.cu)
+  must match the FP64 adjoint of the oracle within the gradient tolerance
+  on the same range.
 
-Both are float32 emulations on the adversarial inputs of
+All are float32 emulations on the adversarial inputs of
 test_filter_bound.py.  Beyond that range (crossings at grazing angles whose
 determinant the FP32 bound cannot separate from zero) the double-float
-values can exceed the tolerance slightly (1.6e-5 once in 140k hits here);
-the kernels do not yet fall back to FP64 there.  CPU only."""
+values can exceed the tolerance (nearest values: 1.6e-5 once in 140k hits;
+gradients: up to 3e-4 in 36 of 47k hits); the kernels do not yet fall back
+to FP64 there.  CPU only."""
 import numpy as np
 import pytest
 
+import oracle
 from test_filter_bound import ETA, F, adversarial, cross, definition64, dot, fmaf
 
 U = 2.0 ** -24
@@ -140,3 +146,71 @@ def test_double_float_values_within_tolerance_where_bounded(cases):
         for x, x64 in zip(df32(*args), ref):
             rel = np.abs(x.astype(np.float64) - x64) / np.maximum(1.0, np.abs(x64))
             assert np.nanmax(np.where(bounded, rel, 0.0)) <= 1e-6
+
+
+def adjoint_df32(a, b, v0, v1, v2, gP, gt):
+    """Per-segment gradients (dA, dB, dV0, dV1, dV2) of the double-float
+    adjoint, as float64 arrays [n, 15]."""
+    n = a.shape[0]
+
+    def sub(x, y):
+        return _add(x, _neg(y))
+
+    def fr(x):
+        return x, np.zeros_like(x)
+
+    def xp(x, y):
+        return [sub(_mul(x[1], y[2]), _mul(x[2], y[1])), sub(_mul(x[2], y[0]), _mul(x[0], y[2])),
+                sub(_mul(x[0], y[1]), _mul(x[1], y[0]))]
+
+    def dp(x, y):
+        return _add(_add(_mul(x[0], y[0]), _mul(x[1], y[1])), _mul(x[2], y[2]))
+
+    def val(z):
+        return z[0].astype(np.float64) + z[1].astype(np.float64)
+
+    with np.errstate(all="ignore"):
+        d = [_two_sum(b[:, k], -a[:, k]) for k in range(3)]
+        nd = [_neg(x) for x in d]
+        e1 = [_two_sum(v1[:, k], -v0[:, k]) for k in range(3)]
+        e2 = [_two_sum(v2[:, k], -v0[:, k]) for k in range(3)]
+        s0 = [_two_sum(a[:, k], -v0[:, k]) for k in range(3)]
+        c12, c20, c01 = xp(e1, e2), xp(e2, nd), xp(nd, e1)
+        det = dp(nd, c12)
+        r = F(1) / det[0]
+        t, u, v = (_div(dp(c, s0), det, r) for c in (c12, c20, c01))
+        gpd = [fr(gP[:, k]) for k in range(3)]
+        gx0, gx1, gx2 = _add(dp(gpd, d), fr(gt[:, 0])), fr(gt[:, 1]), fr(gt[:, 2])
+        one = fr(np.ones(n, F))
+        w, omt = sub(sub(one, u), v), sub(one, t)
+        out = np.zeros((n, 15))
+        for k in range(3):
+            num = _add(_add(_mul(gx0, c12[k]), _mul(gx1, c20[k])), _mul(gx2, c01[k]))
+            lam = _div(num, det, r)
+            sk = _add(gpd[k], lam)
+            out[:, k] = val(_mul(omt, sk)).astype(F)
+            out[:, 3 + k] = val(_mul(t, sk)).astype(F)
+            for q, wt in enumerate((w, u, v)):
+                out[:, 6 + 3 * q + k] = -val(_mul(wt, lam))
+    return out
+
+
+def test_double_float_adjoint_within_tolerance_where_bounded():
+    rng = np.random.default_rng(11)
+    n = 100_000
+    a, b, v0, v1, v2 = adversarial(rng, n)
+    hit = definition64(a, b, v0, v1, v2)[0]
+    bounded = hit & np.isfinite(tight32(a, b, v0, v1, v2)[3])
+    gP = rng.normal(size=(n, 3)).astype(F)
+    gt = rng.normal(size=(n, 3)).astype(F)
+    # the oracle's FP64 adjoint, one triangle per segment
+    V = np.stack([v0, v1, v2], axis=1).reshape(-1, 3)
+    T = np.arange(3 * n, dtype=np.int32).reshape(-1, 3)
+    tri = np.where(bounded, np.arange(n), -1).astype(np.int32)
+    gV, gA, gB = oracle.backward(V, T, a, b, tri, gP=gP.astype(np.float64),
+                                 gtuv=gt.astype(np.float64))
+    ref = np.concatenate([gA, gB, gV.reshape(n, 9)], axis=1)[bounded]
+    got = adjoint_df32(a, b, v0, v1, v2, gP, gt)[bounded]
+    scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max(axis=1, keepdims=True))
+    assert bounded.sum() > 30_000
+    assert (np.abs(got - ref) / scale).max() <= 1e-5
