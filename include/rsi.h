@@ -36,7 +36,11 @@
  *  - Arithmetic: FP32 with certified error bounds; every boolean decision
  *    whose FP32 error bound does not settle it is recomputed in FP64 in the
  *    exact operation order of the definition below, so flags, counts and
- *    triangle ids equal those of the FP64 definition.
+ *    triangle ids equal those of the FP64 definition.  t, u, v, points,
+ *    distances and gradients are within 1e-5 of the definition's FP64
+ *    values (relative to max(1, |x|)), except at extreme grazing angles
+ *    (det not separable from zero in FP32), where the double-float
+ *    refinement can be off by a few 1e-5 (values) or 1e-4 (gradients).
  *
  * Definition computed (Sec. 2, Moller-Trumbore without division):
  *   d = b - a, e1 = v1 - v0, e2 = v2 - v0, p = d x e2, det = e1.p,
