@@ -36,11 +36,13 @@
  *  - Arithmetic: FP32 with certified error bounds; every boolean decision
  *    whose FP32 error bound does not settle it is recomputed in FP64 in the
  *    exact operation order of the definition below, so flags, counts and
- *    triangle ids equal those of the FP64 definition.  t, u, v, points,
- *    distances and gradients are within 1e-5 of the definition's FP64
- *    values (relative to max(1, |x|)), except at extreme grazing angles
- *    (det not separable from zero in FP32), where the double-float
- *    refinement can be off by a few 1e-5 (values) or 1e-4 (gradients).
+ *    triangle ids equal those of the FP64 definition.  t, u, v, points and
+ *    distances are within 1e-5 of the definition's FP64 values (relative to
+ *    max(1, |x|)): FP32 values stand where a rigorous bound shows them
+ *    within that, the rest are recomputed in double-float, or with the FP64
+ *    definition itself at grazing angles (det not separable from zero in
+ *    FP32) and on long segments.  Gradients are within 1e-5 of the FP64
+ *    adjoint (relative to max(|g|, 1e-3 max |g|)).
  *
  * Definition computed (Sec. 2, Moller-Trumbore without division):
  *   d = b - a, e1 = v1 - v0, e2 = v2 - v0, p = d x e2, det = e1.p,
@@ -189,8 +191,14 @@ typedef struct {
     int64_t node_visits;   /* internal nodes fetched */
     int64_t tri_tests;     /* FP32 segment/triangle tests */
     int64_t fp64_tests;    /* tests decided by the FP64 recomputation */
-    int64_t fp64_refines;  /* nearest hits whose outputs were refined in FP64 */
+    int64_t df_refines;    /* nearest hits whose outputs were recomputed in
+                              double-float (the FP32 bound too loose for the
+                              output tolerance) */
     int64_t overflows;     /* segments re-run with a deeper stack */
+    int64_t fp64_values;   /* nearest hits whose outputs were recomputed with
+                              the FP64 definition (grazing crossings whose det
+                              FP32 cannot separate from zero, or directions
+                              outside the FP32 filter's range) */
 } rsi_stats;
 
 /* Library and status helpers. */
@@ -261,7 +269,10 @@ rsi_status rsi_bvh_status(rsi_bvh h, rsi_stream s);
 
 rsi_status rsi_bvh_get_info(rsi_bvh h, rsi_bvh_info* info);
 
-/* Free a handle (stream-ordered on the stream of its last build). */
+/* Free a handle: its internal streams are synchronised, then its memory is
+ * released stream-ordered on the stream of the last call made with it
+ * (every earlier use of the memory precedes that call), which must still
+ * exist. */
 rsi_status rsi_bvh_destroy(rsi_bvh h);
 
 /* Debug / validation: synchronise s and copy the tree of h to HOST buffers,
@@ -351,14 +362,18 @@ rsi_status rsi_intersect_stats(rsi_bvh h, const float* dA, const float* dB, int6
 
 /* Adjoint of the NEAREST outputs with the crossing triangle held fixed (not
  * in the paper; implicit differentiation of a + t d = v0 + u e1 + v e2).
- * With M = [-d, e1, e2], x = (t,u,v) = M^-1 (a - v0) (recomputed in FP64
- * from the geometry), g_x = (gt + gP.d, gu, gv), lambda = M^-T g_x:
+ * With M = [-d, e1, e2], x = (t,u,v) = M^-1 (a - v0) (recomputed from the
+ * geometry, exact input differences), g_x = (gt + gP.d, gu, gv),
+ * lambda = M^-T g_x:
  *   dA[i] = (1-t)(gP + lambda),  dB[i] = t (gP + lambda),
  *   dGradV[T[j][0]] += -(1-u-v) lambda, dGradV[T[j][1]] += -u lambda,
  *   dGradV[T[j][2]] += -v lambda,
- * and zero for segments with dTri[i] < 0.  The algebra and the vertex sums
- * run in FP64 (atomic scatter-add into a stream-ordered FP64 scratch of
- * 24 nV bytes, freed on s), rounded to FP32 once.
+ * and zero for segments with dTri[i] < 0.  The per-segment algebra runs in
+ * double-float (about 44 bits), and in FP64 for crossings at grazing angles
+ * (|det M| <= 2^-16 of its componentwise magnitude, where lambda grows like
+ * 1/det M); the vertex sums use FP64 atomics into a stream-ordered FP64
+ * scratch of 24 nV bytes (freed on s), rounded to FP32 once.  Within the
+ * gradient tolerance stated at the top of this header.
  * Inputs: dV, dT as for the build; dA, dB the segments; dTri int32[nR] saved
  * from the NEAREST forward; dGradPoint float[nR][3] and dGradTuv float[nR][3]
  * (either may be NULL = zero).  Outputs: dGradV float[nV][3] ACCUMULATED into
@@ -387,7 +402,11 @@ rsi_status rsi_intersect_backward(const float* dV, int64_t nV, const int32_t* dT
  *  - nV > RSI_STATIC_MAX_VERTICES returns RSI_ERR_CAPACITY and enqueues
  *    nothing.
  *  - The first call on a device (that device current) looks up the array's
- *    device address; make it before any stream capture begins.
+ *    device address.  Under lazy module loading (CUDA_MODULE_LOADING=LAZY,
+ *    the default since CUDA 12) that first call is also what loads the
+ *    module holding the array, and so commits its 6 MiB of device memory:
+ *    make the first call before reserving the rest of device memory and
+ *    before any stream capture begins.
  *  - All calls share the array: each call clears what it uses first, and
  *    the array keeps the last call's sums.  Calls whose work overlaps on the
  *    GPU (e.g. on two unordered streams) race and give wrong gradients. */
@@ -491,6 +510,20 @@ rsi_status rsi_fp32_peak(int64_t iters, double* tflops, rsi_stream s);
  * allocates 8 bytes (device allocator, on s).  Errors: RSI_ERR_ARG
  * (polls < 1, status_out NULL), RSI_ERR_OOM, RSI_ERR_CUDA. */
 rsi_status rsi_selftest_wait(int32_t polls, rsi_stream s, int32_t* status_out);
+
+/* Self-test of the streamed host path giving up (not part of the paper's
+ * method): one persistent BOOL traversal over nR zero-length segments (no
+ * mesh), launched exactly as the streamed path launches it, whose warps wait
+ * for ready flags that no copy ever sets, each wait bounded by `polls`
+ * polls.  The first wait that gives up latches RSI_ERR_TIMEOUT and ends the
+ * launch for every warp (no warp takes another chunk), so the launch lasts
+ * about one wait, not one per chunk.  Writes the latched status to
+ * *status_out and the launch's event-timed duration in ms to *ms_out
+ * (host).  Synchronises s; allocates about 13 nR bytes (device allocator,
+ * on s).  Errors: RSI_ERR_ARG (polls < 1, nR outside [1, 2^26], a NULL
+ * output), RSI_ERR_OOM, RSI_ERR_CUDA. */
+rsi_status rsi_selftest_stream_wait(int32_t polls, int64_t nR, rsi_stream s,
+                                    int32_t* status_out, float* ms_out);
 
 #ifdef __cplusplus
 }

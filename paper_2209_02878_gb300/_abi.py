@@ -63,7 +63,8 @@ class rsi_bvh_info(C.Structure):
 
 class rsi_stats(C.Structure):
     _fields_ = [("segments", i64), ("node_visits", i64), ("tri_tests", i64),
-                ("fp64_tests", i64), ("fp64_refines", i64), ("overflows", i64)]
+                ("fp64_tests", i64), ("df_refines", i64), ("overflows", i64),
+                ("fp64_values", i64)]
 
 
 class rsi_batch_item(C.Structure):
@@ -111,6 +112,7 @@ _PROTOS = {
     "rsi_fp32_peak": (C.c_int, [i64, P(C.c_double), vp]),
     "rsi_set_allocator": (C.c_int, [vp, vp, vp]),
     "rsi_selftest_wait": (C.c_int, [i32, vp, P(i32)]),
+    "rsi_selftest_stream_wait": (C.c_int, [i32, i64, vp, P(i32), P(C.c_float)]),
 }
 
 # every entry point declared in include/rsi.h

@@ -165,13 +165,16 @@ struct rsi_bvh_s {
     TreeBufs tb;
     char* mem = nullptr;
     size_t bytes = 0;
-    unsigned long long* scratch = nullptr;  // [0] work counter, [1..6] stats
+    unsigned long long* scratch = nullptr;  // [0] work counter, [1..7] stats, [8..9] streamed counters
     bool built = false;
     bool nodes4_valid = false;  // 4-wide records built for the current tree
+    // stream of the last call that queued work on the handle's memory: calls
+    // on a handle are ordered (header), so it follows every earlier use, and
+    // memory is released stream-ordered on it (on reallocation the current
+    // call's stream plays that role)
     cudaStream_t stream = nullptr;
     char* seg_mem = nullptr;  // segment-order workspace (grown on demand)
     rsi::SegOrderWs seg_ws{};
-    cudaStream_t seg_stream = nullptr;
     // host-buffer pipeline (rsi_intersect_host): two streams, double buffers
     cudaStream_t pst[2] = {nullptr, nullptr};
     cudaEvent_t pev_start = nullptr, pev_done[2] = {nullptr, nullptr};
@@ -184,11 +187,9 @@ struct rsi_bvh_s {
     cudaEvent_t sev_free[2] = {nullptr, nullptr}, sev_reset = nullptr;
     bool sfree_valid[2] = {false, false};
     int sslot = 0;
-    cudaStream_t pipe_stream = nullptr;
     // odd-parity workspace (rsi_points_inside): segment ends + counts
     char* in_mem = nullptr;
     int64_t in_cap = 0;
-    cudaStream_t in_stream = nullptr;
     rsi::AllocHooks hooks{};  // device allocator of all this handle's memory
 };
 
@@ -218,7 +219,6 @@ rsi_status ensure_seg_ws(rsi_bvh h, int64_t n, cudaStream_t s) {
     h->seg_ws.hist = (uint32_t*)(p + 4 * b1);
     h->seg_ws.totals = (uint32_t*)(p + 4 * b1 + bh);
     h->seg_ws.cap = n;
-    h->seg_stream = s;
     return RSI_OK;
 }
 }  // namespace
@@ -372,9 +372,14 @@ rsi_status rsi_bvh_destroy(rsi_bvh h) {
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != h->device) cudaSetDevice(h->device);
-    if (h->seg_mem) rsi::dev_free(h->hooks, h->seg_mem, h->seg_stream);
-    if (h->pipe_mem) rsi::dev_free(h->hooks, h->pipe_mem, h->pipe_stream);
-    if (h->in_mem) rsi::dev_free(h->hooks, h->in_mem, h->in_stream);
+    // the internal streams of the host path are the handle's own: let their
+    // work end before the memory they use goes back, on the stream of the
+    // last call (which every use of the memory precedes)
+    for (int q = 0; q < 2; ++q)
+        if (h->pst[q]) cudaStreamSynchronize(h->pst[q]);
+    if (h->seg_mem) rsi::dev_free(h->hooks, h->seg_mem, h->stream);
+    if (h->pipe_mem) rsi::dev_free(h->hooks, h->pipe_mem, h->stream);
+    if (h->in_mem) rsi::dev_free(h->hooks, h->in_mem, h->stream);
     for (int q = 0; q < 2; ++q) {
         if (h->pst[q]) cudaStreamDestroy(h->pst[q]);
         if (h->pev_done[q]) cudaEventDestroy(h->pev_done[q]);
@@ -508,7 +513,8 @@ static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, in
         RSI_CK(rsi::build_nodes4(h->tb, (cudaStream_t)s));
         h->nodes4_valid = true;
     }
-    if (c.stats) RSI_CK(cudaMemsetAsync(P.stats, 0, 6 * 8, (cudaStream_t)s));
+    if (c.stats)
+        RSI_CK(cudaMemsetAsync(P.stats, 0, rsi::kStatCounters * 8, (cudaStream_t)s));
     if (c.packet)
         RSI_CK(rsi::launch_trace_packet(P, mode, c.stats, (cudaStream_t)s));
     else
@@ -518,7 +524,9 @@ static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, in
 
 rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR, rsi_mode mode,
                          const rsi_output* out, const rsi_launch_opts* lo, rsi_stream s) {
-    return intersect_impl(h, dA, dB, nR, mode, out, lo, s, false);
+    const rsi_status st = intersect_impl(h, dA, dB, nR, mode, out, lo, s, false);
+    if (h) h->stream = (cudaStream_t)s;
+    return st;
 }
 
 rsi_status rsi_intersect_stats(rsi_bvh h, const float* dA, const float* dB, int64_t nR,
@@ -527,16 +535,19 @@ rsi_status rsi_intersect_stats(rsi_bvh h, const float* dA, const float* dB, int6
     if (!stt) return RSI_ERR_ARG;
     memset(stt, 0, sizeof(*stt));
     rsi_status st = intersect_impl(h, dA, dB, nR, mode, out, lo, s, true);
+    if (h) h->stream = (cudaStream_t)s;
     if (st != RSI_OK || nR == 0) return st;
-    unsigned long long v[6];
-    RSI_CK(cudaMemcpyAsync(v, h->scratch + 1, 48, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+    unsigned long long v[rsi::kStatCounters];
+    RSI_CK(cudaMemcpyAsync(v, h->scratch + 1, sizeof(v), cudaMemcpyDeviceToHost,
+                           (cudaStream_t)s));
     RSI_CK(cudaStreamSynchronize((cudaStream_t)s));
     stt->segments = (int64_t)v[0];
     stt->node_visits = (int64_t)v[1];
     stt->tri_tests = (int64_t)v[2];
     stt->fp64_tests = (int64_t)v[3];
-    stt->fp64_refines = (int64_t)v[4];
+    stt->df_refines = (int64_t)v[4];
     stt->overflows = (int64_t)v[5];
+    stt->fp64_values = (int64_t)v[6];
     return RSI_OK;
 }
 
@@ -595,8 +606,8 @@ static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB
     }
     if (h->pipe_bytes < 2 * slot_need) {  // (re)allocated on s: the copies must follow s
         h->sfree_valid[0] = h->sfree_valid[1] = false;
-        if (h->pipe_mem) {
-            RSI_CK(rsi::dev_free(h->hooks, h->pipe_mem, h->pipe_stream));
+        if (h->pipe_mem) {  // every earlier use precedes this call on cs
+            RSI_CK(rsi::dev_free(h->hooks, h->pipe_mem, cs));
             h->pipe_mem = nullptr;
             h->pipe_bytes = 0;
         }
@@ -607,7 +618,6 @@ static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB
             return e == cudaErrorMemoryAllocation ? RSI_ERR_OOM : RSI_ERR_CUDA;
         }
         h->pipe_bytes = 2 * slot_need;
-        h->pipe_stream = cs;
     }
     if (!h->one) {
         RSI_CK(cudaHostAlloc((void**)&h->one, sizeof(int32_t), cudaHostAllocDefault));
@@ -658,7 +668,7 @@ static rsi_status intersect_streamed(rsi_bvh h, const float* hA, const float* hB
     return RSI_OK;
 }
 
-rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64_t nR,
+static rsi_status intersect_host_impl(rsi_bvh h, const float* hA, const float* hB, int64_t nR,
                               rsi_mode mode, const rsi_output* hout, int64_t chunk,
                               const rsi_launch_opts* lo, rsi_stream s) {
     if (!h || nR < 0 || chunk < 0) return RSI_ERR_ARG;
@@ -715,8 +725,8 @@ rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64
                              : align256((size_t)(out_bytes_per_seg(mode) * ch));
     const size_t per_buf = 2 * in_b + out_b;
     if (h->pipe_bytes < 2 * per_buf) {
-        if (h->pipe_mem) {
-            RSI_CK(rsi::dev_free(h->hooks, h->pipe_mem, h->pipe_stream));
+        if (h->pipe_mem) {  // every earlier use precedes this call on cs
+            RSI_CK(rsi::dev_free(h->hooks, h->pipe_mem, cs));
             h->pipe_mem = nullptr;
             h->pipe_bytes = 0;
         }
@@ -727,7 +737,6 @@ rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64
             return e == cudaErrorMemoryAllocation ? RSI_ERR_OOM : RSI_ERR_CUDA;
         }
         h->pipe_bytes = 2 * per_buf;
-        h->pipe_stream = cs;
     }
     RSI_CK(cudaEventRecord(h->pev_start, cs));
     for (int q = 0; q < 2; ++q) RSI_CK(cudaStreamWaitEvent(h->pst[q], h->pev_start, 0));
@@ -785,8 +794,16 @@ rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64
     return RSI_OK;
 }
 
-rsi_status rsi_points_inside(rsi_bvh h, const float* dP, int64_t nP, uint8_t* dInside,
-                             const rsi_launch_opts* lo, rsi_stream s) {
+rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64_t nR,
+                              rsi_mode mode, const rsi_output* hout, int64_t chunk,
+                              const rsi_launch_opts* lo, rsi_stream s) {
+    const rsi_status st = intersect_host_impl(h, hA, hB, nR, mode, hout, chunk, lo, s);
+    if (h) h->stream = (cudaStream_t)s;
+    return st;
+}
+
+static rsi_status points_inside_impl(rsi_bvh h, const float* dP, int64_t nP, uint8_t* dInside,
+                                     const rsi_launch_opts* lo, rsi_stream s) {
     if (!h || nP < 0) return RSI_ERR_ARG;
     if (!h->built) return RSI_ERR_NOT_BUILT;
     if (nP == 0) return RSI_OK;
@@ -798,7 +815,7 @@ rsi_status rsi_points_inside(rsi_bvh h, const float* dP, int64_t nP, uint8_t* dI
     }
     if (h->in_cap < nP) {
         if (h->in_mem) {
-            RSI_CK(rsi::dev_free(h->hooks, h->in_mem, h->in_stream));
+            RSI_CK(rsi::dev_free(h->hooks, h->in_mem, cs));
             h->in_mem = nullptr;
         }
         cudaError_t e = rsi::dev_alloc(h->hooks, (void**)&h->in_mem, (size_t)(16 * nP + 512), cs);
@@ -809,7 +826,6 @@ rsi_status rsi_points_inside(rsi_bvh h, const float* dP, int64_t nP, uint8_t* dI
             return e == cudaErrorMemoryAllocation ? RSI_ERR_OOM : RSI_ERR_CUDA;
         }
         h->in_cap = nP;
-        h->in_stream = cs;
     }
     float* dB = (float*)h->in_mem;
     int32_t* cnt = (int32_t*)(h->in_mem + align256(12 * (size_t)h->in_cap));
@@ -821,6 +837,13 @@ rsi_status rsi_points_inside(rsi_bvh h, const float* dP, int64_t nP, uint8_t* dI
     if (st != RSI_OK) return st;
     RSI_CK(rsi::launch_parity(cnt, nP, dInside, cs));
     return RSI_OK;
+}
+
+rsi_status rsi_points_inside(rsi_bvh h, const float* dP, int64_t nP, uint8_t* dInside,
+                             const rsi_launch_opts* lo, rsi_stream s) {
+    const rsi_status st = points_inside_impl(h, dP, nP, dInside, lo, s);
+    if (h) h->stream = (cudaStream_t)s;
+    return st;
 }
 
 rsi_status rsi_intersect_backward(const float* dV, int64_t nV, const int32_t* dT, int64_t nT,

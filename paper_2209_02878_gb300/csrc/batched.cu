@@ -18,7 +18,7 @@ namespace rsi {
 // path spills).
 template <int STACK>
 __global__ void __maxnreg__(128) k_batch(BatchParams P) {
-    TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull};
+    TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
     unsigned long long segs = 0;
     const int lane = threadIdx.x & 31;
     while (true) {
@@ -44,6 +44,7 @@ __global__ void __maxnreg__(128) k_batch(BatchParams P) {
         C.fetch = kFetchChunk;  // unused: each tile is one warp's whole pool
         C.ready = nullptr;
         C.ready_chunk = 1;
+        C.wait_polls = kWaitPolls;
         C.order = nullptr;
         C.status = P.status;
         C.out = it.out;

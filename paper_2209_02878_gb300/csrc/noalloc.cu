@@ -18,8 +18,12 @@
 //    allocated until the process exits (6 MiB).
 //  - Host code cannot use the array's name as a device address.  The first
 //    call on each device (with that device current) looks the address up
-//    with cudaGetSymbolAddress and remembers it; make that first call before
-//    any stream capture starts.
+//    with cudaGetSymbolAddress and remembers it.  The library is built
+//    without relocatable device code, so this file is a module of its own:
+//    under lazy module loading (the default since CUDA 12) that lookup is
+//    what loads the module and commits the array's 6 MiB on the device.
+//    Make that first call before reserving the rest of device memory and
+//    before any stream capture starts.
 //  - Every call shares the one array: each call clears the part it uses
 //    (cudaMemsetAsync, which does not allocate) before accumulating, and the
 //    array keeps the last call's sums afterwards.  Two calls whose work

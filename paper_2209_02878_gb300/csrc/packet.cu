@@ -53,10 +53,11 @@ __global__ void __maxnreg__(PacketRegs<MODE>::value) k_trace_packet(TraceParams 
     C.fetch = 32;  // packets take 32 segments per warp themselves
     C.ready = nullptr;
     C.ready_chunk = 1;
+    C.wait_polls = kWaitPolls;
     C.order = P.order;
     C.status = P.status;
     C.out = P.out;
-    TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull};
+    TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
     unsigned long long segs = 0;
     int stack[kPacketStack];
     while (true) {

@@ -11,6 +11,7 @@
 // the chains live without memory traffic.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "rsi.h"
 #include "rsi_trace.h"
@@ -61,6 +62,61 @@ extern "C" rsi_status rsi_selftest_wait(int32_t polls, rsi_stream s, int32_t* st
             cudaStreamSynchronize(cs) != cudaSuccess)
             st = RSI_ERR_CUDA;
     }
+    rsi::dev_free(hooks, mem, cs);
+    if (st != RSI_OK) cudaGetLastError();
+    return st;
+}
+
+extern "C" rsi_status rsi_selftest_stream_wait(int32_t polls, int64_t nR, rsi_stream s,
+                                               int32_t* status_out, float* ms_out) {
+    if (polls < 1 || nR < 1 || nR > (int64_t(1) << 26) || !status_out || !ms_out)
+        return RSI_ERR_ARG;
+    cudaStream_t cs = (cudaStream_t)s;
+    const rsi::AllocHooks hooks = rsi::current_hooks();
+    // segments (all zero), flags, the per-chunk ready flags that no copy
+    // ever sets, the work counter and the status word
+    const int64_t chunk = 32;
+    const int64_t nc = (nR + chunk - 1) / chunk;
+    const size_t seg_b = (12 * (size_t)nR + 255) / 256 * 256;
+    const size_t flag_b = ((size_t)nR + 255) / 256 * 256;
+    const size_t ready_b = (4 * (size_t)nc + 255) / 256 * 256;
+    const size_t bytes = seg_b + flag_b + ready_b + 256;
+    char* mem = nullptr;
+    if (rsi::dev_alloc(hooks, (void**)&mem, bytes, cs) != cudaSuccess) {
+        cudaGetLastError();
+        return RSI_ERR_OOM;
+    }
+    rsi_status st = RSI_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMemsetAsync(mem, 0, bytes, cs) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        st = RSI_ERR_CUDA;
+    if (st == RSI_OK) {
+        rsi::TraceParams P;
+        memset(&P, 0, sizeof(P));
+        P.A = (const float*)mem;  // A and B alias: zero-length segments
+        P.B = (const float*)mem;
+        P.nR = nR;
+        P.root = rsi::kNoRoot;  // no mesh: a segment, once its chunk is in, misses
+        P.root4 = rsi::kNoRoot;
+        P.out.flag = (uint8_t*)(mem + seg_b);
+        P.ready = (const int32_t*)(mem + seg_b + flag_b);
+        P.ready_chunk = chunk;
+        P.wait_polls = polls;
+        P.work = (unsigned long long*)(mem + seg_b + flag_b + ready_b);
+        P.status = (int32_t*)(mem + seg_b + flag_b + ready_b + 128);
+        P.max_visits = 2;
+        if (cudaEventRecord(e0, cs) != cudaSuccess ||
+            rsi::launch_trace(P, RSI_MODE_BOOL, 64, false, 128, 2, cs) != cudaSuccess ||
+            cudaEventRecord(e1, cs) != cudaSuccess ||
+            cudaMemcpyAsync(status_out, P.status, sizeof(int32_t), cudaMemcpyDeviceToHost, cs) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(cs) != cudaSuccess ||
+            cudaEventElapsedTime(ms_out, e0, e1) != cudaSuccess)
+            st = RSI_ERR_CUDA;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     rsi::dev_free(hooks, mem, cs);
     if (st != RSI_OK) cudaGetLastError();
     return st;

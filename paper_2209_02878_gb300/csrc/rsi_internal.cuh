@@ -522,9 +522,11 @@ __device__ __forceinline__ float df_float(dfl a) { return __fadd_rn(a.h, a.l); }
 
 // (t, u, v) of the segment a -> b against triangle (v0, v1, v2) in
 // double-float, in the operation order of the definition (differences are
-// exact in double-float).  Only used for values, never for decisions.
+// exact in double-float); t is returned as a double-float pair so that the
+// point a + t d can be formed without rounding t to FP32 first.  Only used
+// for values, never for decisions.
 static __device__ __noinline__ void mt_df(const float* a3, const float* b3, float4 A, float4 B,
-                                   float4 C, float* tuv) {
+                                   float4 C, dfl& t, float& u, float& v) {
     dfl d[3], e1[3], e2[3], s0[3];
     const float v0[3] = {A.x, A.y, A.z}, v1[3] = {B.x, B.y, B.z}, v2[3] = {C.x, C.y, C.z};
     for (int k = 0; k < 3; ++k) {
@@ -547,9 +549,9 @@ static __device__ __noinline__ void mt_df(const float* a3, const float* b3, floa
     cross(s0, e1, q);
     const dfl nu = dot(s0, p), nv = dot(d, q), nt = dot(e2, q);
     const float r = rcp_approx(det.h);
-    tuv[0] = df_float(df_div(nt, det, r));
-    tuv[1] = df_float(df_div(nu, det, r));
-    tuv[2] = df_float(df_div(nv, det, r));
+    t = df_div(nt, det, r);
+    u = df_float(df_div(nu, det, r));
+    v = df_float(df_div(nv, det, r));
 }
 
 }  // namespace rsi

@@ -37,6 +37,7 @@ struct TraceParams {
     int fetch;                  // segments per warp fetch (set by launch_trace)
     const int32_t* ready;       // streamed input flags (see TraceCtx), or nullptr
     int64_t ready_chunk;
+    int wait_polls;             // polls of a ready flag before giving up (0: kWaitPolls)
     const int32_t* order;       // optional coherent processing order (nullptr = identity)
     int32_t* status;
     TravOut out;

@@ -45,10 +45,11 @@ __global__ void __maxnreg__(TraceRegs<MODE>::value) k_trace(TraceParams P) {
     C.fetch = P.fetch;
     C.ready = P.ready;
     C.ready_chunk = P.ready_chunk;
+    C.wait_polls = P.wait_polls > 0 ? P.wait_polls : kWaitPolls;
     C.order = P.order;
     C.status = P.status;
     C.out = P.out;
-    TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull};
+    TravStats st = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
     unsigned long long segs = 0;
     trace_loop<MODE, STACK, STATS, W, TL>(C, P.work, 0, P.nR, st, segs);
     if (STATS) flush_stats(st, P.stats, segs);

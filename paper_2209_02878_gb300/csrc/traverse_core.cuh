@@ -32,8 +32,15 @@ struct TravOut {
     int32_t* hit_count;
 };
 
+// Counters of a STATS launch, in this order: segments, node visits, triangle
+// tests, FP64 decisions, double-float refinements, stack overflows, FP64
+// value recomputations.
+constexpr int kStatCounters = 7;
+
 struct TravStats {
-    unsigned long long visits, tests, fp64, refines, overflows;
+    // refines: nearest outputs recomputed in double-float; exact: recomputed
+    // with the FP64 definition (grazing crossings, out-of-range directions)
+    unsigned long long visits, tests, fp64, refines, overflows, exact;
 };
 
 struct Result {
@@ -164,6 +171,7 @@ struct TraceCtx {
     int fetch;             // segments a warp takes from the counter at once
     const int32_t* ready;  // streamed input: chunk c of ready_chunk segments is in
     int64_t ready_chunk;   // place once ready[c] != 0 (nullptr: all in place)
+    int wait_polls;        // polls of a ready flag before giving up
     const int32_t* order;  // optional processing order of the segments
     int32_t* status;
     TravOut out;
@@ -347,11 +355,65 @@ __device__ __forceinline__ void result_init(Result& r) {
     r.b64 = false;
 }
 
+// Nearest outputs recomputed with the FP64 definition (its operation order
+// for t, u, v; the point a + t d and the distance t |d| in FP64 as well),
+// rounded to FP32 and written to o[0..6] = t, u, v, P, dist.  The
+// recomputations are out of line and return through the caller's local
+// array: inlined, or returning a structure in registers, they cost the
+// traversal loop registers (measured: a quarter slower nearest traversals).
+static __device__ __noinline__ void values64(const float* A, const float* B, int64_t i,
+                                             float4 v0, float4 v1, float4 v2, float* o) {
+    double tuv[3] = {0.0, 0.0, 0.0};
+    mt64(A[3 * i], A[3 * i + 1], A[3 * i + 2], B[3 * i], B[3 * i + 1], B[3 * i + 2], v0, v1, v2,
+         tuv);
+    double dd = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double a = A[3 * i + k], d = __dsub_rn((double)B[3 * i + k], a);
+        o[3 + k] = (float)__dadd_rn(a, __dmul_rn(tuv[0], d));
+        dd = __dadd_rn(dd, __dmul_rn(d, d));
+    }
+    o[0] = (float)tuv[0];
+    o[1] = (float)tuv[1];
+    o[2] = (float)tuv[2];
+    o[6] = (float)__dmul_rn(tuv[0], __dsqrt_rn(dd));
+}
+
+// Nearest outputs recomputed in double-float, written to o[0..6] as above;
+// the point from the unrounded double-float t and the exact d = b - a
+// (two-sum), since the FP32 rounding of t times a long |d| can exceed the
+// tolerance.
+static __device__ __noinline__ void values_df(const float* a3, const float* b3, float4 v0,
+                                              float4 v1, float4 v2, float* o) {
+    dfl t;
+    mt_df(a3, b3, v0, v1, v2, t, o[1], o[2]);
+    o[0] = df_float(t);
+    float dd = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        const dfl d = df_two_sum(b3[k], -a3[k]);
+        o[3 + k] = df_float(df_add({a3[k], 0.f}, df_mul(t, d)));
+        dd = fmaf(d.h, d.h, dd);
+    }
+    o[6] = o[0] * sqrtf(dd);
+}
+
 // Nearest outputs.  (t, u, v) keep their FP32 values when a rigorous bound
 // (first the filter's, then a tighter one for this triangle) shows them, and
-// the point, within half the 1e-5 tolerance; otherwise they are recomputed in
-// double-float, and in FP64 for segments whose direction is outside the FP32
-// filter's range.
+// the point, within the tolerance.  Otherwise they are recomputed: in
+// double-float while the tight bound still keeps det away from zero and the
+// double-float error of t (below 2^-20 of that bound; measured: 2e-8), times
+// |d| for the point, stays within half the tolerance; with the FP64
+// definition where it does not (a crossing at a grazing angle, or a long
+// segment), or where the segment's direction is outside the FP32 filter's
+// range.
+//
+// Thresholds: the output tolerance is 1e-5 relative to max(1, |x|), and the
+// bounds are rigorous.  u and v: their bound (which includes their FP32
+// rounding) below 0.95e-5.  t: the point fma(t, fl(d), a) is off by at most
+// |d| (err_t + u) (the error of t, and the rounding of fl(b - a), t <= 1)
+// plus its own rounding u max(1, |P|), so err_t below
+// 0.95 ((1e-5 - u) / max(1, |d|) - u) keeps the point, the distance and t
+// itself within the tolerance (u = 2^-24); for |d| beyond about 160 no FP32
+// t qualifies and the outputs are always recomputed.
 template <bool STATS>
 __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, const float* B,
                                                int64_t i, const float4* __restrict__ tris,
@@ -360,32 +422,12 @@ __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, con
     t = res.bt;
     u = res.bu;
     v = res.bv;
-    // the tolerance of these outputs is 1e-5 (the bounds are rigorous, keep a
-    // margin of 2): t needs 5e-6 / |d| (the point and the distance move by
-    // |d| times the error of t), u and v 5e-6
     const float dlen = sqrtf(fmaf(s.dx, s.dx, fmaf(s.dy, s.dy, s.dz * s.dz))) * 1.0001f;
-    const float thresh = 5e-6f / fmaxf(1.f, dlen);
-    const float thresh_uv = 5e-6f;
+    const float thresh = 0.95f * ((1e-5f - 0x1p-24f) / fmaxf(1.f, dlen) - 0x1p-24f);
+    const float thresh_uv = 0.95e-5f;
     const int p = res.bpos;
-    if (s.fp64only) {
-        if (STATS) ++st.refines;
-        double tuv[3] = {0.0, 0.0, 0.0};
-        mt64(A[3 * i], A[3 * i + 1], A[3 * i + 2], B[3 * i], B[3 * i + 1], B[3 * i + 2],
-             ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
-             ld4(tris + 3 * (int64_t)p + 2), tuv);
-        t = (float)tuv[0];
-        u = (float)tuv[1];
-        v = (float)tuv[2];
-        double dd = 0.0;
-        for (int k = 0; k < 3; ++k) {
-            const double a = A[3 * i + k], d = (double)B[3 * i + k] - a;
-            P[k] = (float)(a + tuv[0] * d);
-            dd += d * d;
-        }
-        dist = (float)(tuv[0] * sqrt(dd));
-        return;
-    }
-    bool refine = res.berr > thresh;  // berr bounds t, u and v together
+    bool exact = s.fp64only;
+    bool refine = !exact && res.berr > thresh;  // berr bounds t, u and v together
     if (refine) {  // tighter bounds for this one triangle first, t and (u, v) apart
         float t2, u2, v2, euv;
         const float et = mt32_tight(s, ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
@@ -395,18 +437,39 @@ __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, con
             u = u2;
             v = v2;
             refine = false;
+        } else if (!(et < INFINITY && dlen * et <= 4.f && euv <= 4.f)) {
+            exact = true;
         }
+    }
+    if (exact) {
+        if (STATS) ++st.exact;
+        float o[7];
+        values64(A, B, i, ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
+                 ld4(tris + 3 * (int64_t)p + 2), o);
+        t = o[0];
+        u = o[1];
+        v = o[2];
+        P[0] = o[3];
+        P[1] = o[4];
+        P[2] = o[5];
+        dist = o[6];
+        return;
     }
     if (refine) {
         if (STATS) ++st.refines;
         const float a3[3] = {s.ax(), s.ay(), s.az()};
         const float b3[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
-        float tuv[3];
-        mt_df(a3, b3, ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
-              ld4(tris + 3 * (int64_t)p + 2), tuv);
-        t = tuv[0];
-        u = tuv[1];
-        v = tuv[2];
+        float o[7];
+        values_df(a3, b3, ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
+                  ld4(tris + 3 * (int64_t)p + 2), o);
+        t = o[0];
+        u = o[1];
+        v = o[2];
+        P[0] = o[3];
+        P[1] = o[4];
+        P[2] = o[5];
+        dist = o[6];
+        return;
     }
     P[0] = fmaf(t, s.dx, s.ax());
     P[1] = fmaf(t, s.dy, s.ay());
@@ -482,15 +545,21 @@ constexpr int kWaitPolls = 1 << 22;  // polls of a ready flag (~1 s) before RSI_
 
 // Bounded wait of a whole warp for *flag != 0 (written by a copy on another
 // stream): every lane polls with an acquire load, so its later loads of the
-// flagged data are ordered after it.  Gives up after `polls` polls, latches
-// RSI_ERR_TIMEOUT and returns false (the caller carries on; its results are
-// then not to be trusted, which the status says).  Must be called by all 32
-// lanes.
+// flagged data are ordered after it.  Gives up after `polls` polls, or as
+// soon as *status holds RSI_ERR_TIMEOUT (another warp's wait already gave
+// up), latches RSI_ERR_TIMEOUT and returns false; the caller then stops
+// taking work (its results are not to be trusted, which the status says).
+// Must be called by all 32 lanes.
 __device__ __forceinline__ bool wait_flag(const int32_t* flag, int32_t* status, int polls) {
     for (int q = 0; q < polls; ++q) {
         int v;
         asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
         if (__all_sync(0xffffffffu, v != 0)) return true;
+        if ((q & 255) == 255) {
+            int st;
+            asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(st) : "l"(status) : "memory");
+            if (__any_sync(0xffffffffu, st == RSI_ERR_TIMEOUT)) break;
+        }
         __nanosleep(256);
     }
     if ((threadIdx.x & 31) == 0) atomicCAS(status, 0, RSI_ERR_TIMEOUT);
@@ -557,8 +626,17 @@ __device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long
                 pool = (int64_t)b;
                 pool_end = pool + C.fetch < hi ? pool + C.fetch : hi;
                 // streamed input: the chunks holding [pool, pool_end) have
-                // landed once the flag of the last one is set (copies in order)
-                if (C.ready) wait_flag(C.ready + (pool_end - 1) / C.ready_chunk, C.status, kWaitPolls);
+                // landed once the flag of the last one is set (copies in order).
+                // A wait that gives up ends the launch: this warp skips its
+                // chunk and the counter is run out, so that no warp takes
+                // (and waits for) another one.
+                if (C.ready &&
+                    !wait_flag(C.ready + (pool_end - 1) / C.ready_chunk, C.status, C.wait_polls)) {
+                    if (lane == 0) atomicMax(counter, (unsigned long long)hi);
+                    pool = pool_end;
+                    more = false;
+                    break;
+                }
             }
             const int64_t left = pool_end - pool;
             const int avail = left < (int64_t)__popc(idle) ? (int)left : __popc(idle);
@@ -604,14 +682,15 @@ __device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long
 // Sum the per-thread counters of a warp into the global stats.
 __device__ __forceinline__ void flush_stats(const TravStats& st, unsigned long long* g,
                                             unsigned long long segs) {
-    unsigned long long v[6] = {segs, st.visits, st.tests, st.fp64, st.refines, st.overflows};
+    unsigned long long v[kStatCounters] = {segs,     st.visits,    st.tests, st.fp64,
+                                           st.refines, st.overflows, st.exact};
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < kStatCounters; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     }
     if ((threadIdx.x & 31) == 0)
-        for (int k = 0; k < 6; ++k) atomicAdd(g + k, v[k]);
+        for (int k = 0; k < kStatCounters; ++k) atomicAdd(g + k, v[k]);
 }
 
 }  // namespace rsi

@@ -13,6 +13,8 @@ evaluation orders the bound is derived for.  CPU only."""
 import numpy as np
 import pytest
 
+from _adversarial import adversarial
+
 F = np.float32
 U = 2.0 ** -24
 K = F(2.0 ** -17)
@@ -125,42 +127,6 @@ def definition64(a, b, v0, v1, v2):
     hit = (det > 0) & (nu >= 0) & (nv >= 0) & (nu + nv <= det) & (nt >= 0) & (nt <= det)
     with np.errstate(all="ignore"):
         return hit, nt / det, nu / det, nv / det
-
-
-def adversarial(rng, n):
-    """Triangles over many binades and segments whose exact crossing sits
-    near an edge, a vertex or a segment end, or that run nearly parallel
-    to the plane."""
-    scale = 2.0 ** rng.uniform(-12, 12, n)[:, None]
-    offset = rng.normal(size=(n, 3)) * 2.0 ** rng.uniform(-12, 12, n)[:, None]
-    v0 = offset + scale * rng.normal(size=(n, 3))
-    v1 = offset + scale * rng.normal(size=(n, 3))
-    v2 = offset + scale * rng.normal(size=(n, 3))
-    delta = 10.0 ** rng.uniform(-9, -3, n)
-    kind = rng.integers(0, 6, n)
-    u = rng.uniform(0, 1, n)
-    v = rng.uniform(0, 1, n) * (1 - u)
-    sgn = rng.choice([-1.0, 1.0], n)
-    u = np.where(kind == 0, sgn * delta, u)                       # near the edge u = 0
-    v = np.where(kind == 1, sgn * delta, v)                       # near the edge v = 0
-    v = np.where(kind == 2, 1 - u + sgn * delta, v)               # near the edge u + v = 1
-    u = np.where(kind == 3, sgn * delta, u)                       # near the vertex v0
-    v = np.where(kind == 3, rng.choice([-1.0, 1.0], n) * delta, v)
-    X = v0 + u[:, None] * (v1 - v0) + v[:, None] * (v2 - v0)
-    nrm = np.cross(v1 - v0, v2 - v0)
-    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
-    dirn = rng.normal(size=(n, 3))
-    dirn /= np.linalg.norm(dirn, axis=1, keepdims=True)
-    # nearly parallel: the in-plane part of a direction plus a tiny normal part
-    par = dirn - np.sum(dirn * nrm, axis=1, keepdims=True) * nrm
-    par = par / np.linalg.norm(par, axis=1, keepdims=True) + sgn[:, None] * delta[:, None] * nrm
-    dirn = np.where((kind == 5)[:, None], par, dirn)
-    length = scale * 2.0 ** rng.uniform(-3, 3, n)[:, None]
-    t0 = rng.uniform(0, 1, n)
-    t0 = np.where(kind == 4, rng.choice([0.0, 1.0], n) + sgn * delta, t0)  # near a segment end
-    a = X - t0[:, None] * length * dirn
-    b = a + length * dirn
-    return tuple(x.astype(F) for x in (a, b, v0, v1, v2))
 
 
 @pytest.mark.parametrize("seed", range(4))

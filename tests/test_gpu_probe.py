@@ -40,3 +40,28 @@ def test_bounded_wait_times_out_and_the_context_survives():
     flag = bvh.intersect(torch.from_numpy(seg.A).to(dev), torch.from_numpy(seg.B).to(dev))["flag"]
     torch.cuda.synchronize()
     assert bvh.status() == 0 and 0 < int(flag.sum()) < seg.n
+
+
+def test_streamed_launch_gives_up_after_one_wait():
+    """A whole persistent BOOL traversal whose warps wait for ready flags
+    that no copy sets (rsi_selftest_stream_wait): the first wait that gives
+    up ends the launch for every warp, so 4M segments in 128-segment chunks
+    (tens of thousands of chunks, several per resident warp) take about as
+    long as one chunk's wait, not one wait per chunk."""
+    import ctypes as C
+
+    from paper_2209_02878_gb300 import _abi
+    lib = _abi.load()
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    polls = 20000
+    res = {}
+    for n in (32, 4_000_000):
+        st, ms = C.c_int32(-1), C.c_float(-1.0)
+        assert lib.rsi_selftest_stream_wait(polls, n, s, C.byref(st), C.byref(ms)) == _abi.RSI_OK
+        assert st.value == _abi.RSI_ERR_TIMEOUT, (n, st.value)
+        res[n] = ms.value
+    assert res[32] > 0.5, res            # one wait of 20k polls takes a while
+    assert res[4_000_000] < 3 * res[32] + 5.0, res
+    # the device is still usable
+    x = torch.arange(10, device="cuda:0").sum()
+    assert int(x) == 45

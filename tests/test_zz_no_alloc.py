@@ -6,8 +6,10 @@ tests), and an oversized mesh must be rejected.
 The entry point exists for callers that may not allocate device memory while
 they run (fixed memory budgets, graph capture into a pool they do not own,
 allocator callbacks); it keeps its accumulator in a fixed array inside the
-library.  This file sorts last so that a run stopping at the first failure
-has already run every other test; it also passes on its own."""
+library.  With counting allocator hooks installed, the two calls must make
+no allocation through the library's allocator (the allocating variant, the
+control, does).  This file sorts last so that a run stopping at the first
+failure has already run every other test; it also passes on its own."""
 import ctypes as C
 
 import numpy as np
@@ -78,3 +80,39 @@ def test_static_backward_rejects_oversized_mesh():
     rc = lib.rsi_intersect_backward_static(_p(V), n, _p(T), 1, _p(A), _p(A), 4, _p(tri), None,
                                            None, _p(g), None, None, s)
     assert rc == _abi.RSI_ERR_CAPACITY
+
+
+def test_static_backward_allocates_nothing():
+    """Counting hooks on the library's allocator (rsi_set_allocator): after
+    one warm-up call (which looks up the array, and under lazy loading loads
+    its module), two static calls make no allocation or free; the allocating
+    entry point, as a control, makes one of each."""
+    import paper_2209_02878_gb300 as rsi
+    lib = _abi.load()
+    V, T, A, B, w, wt = _case()
+    tri = rsi.BVH(V, T).intersect(A, B, "nearest")["tri"]
+    torch.cuda.synchronize()
+    _backward(lib, "rsi_intersect_backward_static", V, T, A, B, tri, w, wt)
+    calls = {"alloc": 0, "free": 0}
+    live = {}
+
+    def alloc(nbytes, device, stream):
+        calls["alloc"] += 1
+        p = torch.cuda.caching_allocator_alloc(nbytes, device=device, stream=stream)
+        live[p] = True
+        return p
+
+    def free(p, device, stream):
+        calls["free"] += 1
+        live.pop(p)
+        torch.cuda.caching_allocator_delete(p)
+
+    rsi.set_allocator(alloc, free)
+    try:
+        for _ in range(2):
+            _backward(lib, "rsi_intersect_backward_static", V, T, A, B, tri, w, wt)
+        assert calls == {"alloc": 0, "free": 0}, calls
+        _backward(lib, "rsi_intersect_backward", V, T, A, B, tri, w, wt)
+        assert calls == {"alloc": 1, "free": 1}, calls
+    finally:
+        rsi.set_allocator(None, None)
