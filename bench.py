@@ -36,9 +36,9 @@ WORKLOAD = "heightfield 123x123 (29,768 tris) x 10M segments, boolean, build+tra
 BYTES_PER_SEG_BOOL = 25     # 24 B of segment endpoints in + 1 B flag out
 BYTES_PER_SEG_NEAREST = 64  # 24 B in + tri, t, u, v, point, dist (40 B) out
 BYTES_PER_SEG_COUNT = 28
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_trace<BOOL> launch on
-# this workload (ncu, profiles/k_trace_bool_paper_scale.md), valid while the
-# traversal sources hash to `sha`; otherwise reported as null
+# dram__bytes_read.sum + dram__bytes_write.sum and warp instructions of one
+# k_trace<BOOL> launch on this workload, from an ncu capture of the traversal
+# built from sources hashing to `sha`; reported as null once they differ
 TRAFFIC = {"sha": "13251166776d4519", "bytes": 258_686_208, "warp_inst": 961_160_469}
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle at
 # the maximum SM clock (2,070 MHz)
@@ -178,6 +178,15 @@ def cpu_oracle_rate(mesh, seg, target_s=12.0, max_n=10_000_000):
         if dt >= target_s or n >= max_n or total > 3 * target_s:
             return n / dt / 1e6, threads, n, dt
         n = min(max_n, int(n * max(2.0, min(20.0, target_s / max(dt, 1e-3)))))
+
+
+def neardeg_rate(mesh, seg, n=200_000):
+    """Share of near-degenerate segments among the first n (the oracle's
+    flag), with the sample size."""
+    import oracle
+    n = min(n, seg.n)
+    r = oracle.CpuBVH(mesh.V, mesh.T).query(seg.A[:n], seg.B[:n], threads=oracle.num_threads())
+    return {"value": float(r["neardeg"].mean()), "sample": n}
 
 
 # ------------------------------------------------------------------ arms
@@ -331,6 +340,13 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, thr, n, dt = cpu_oracle_rate(mesh, seg)
         rate1, n1, dt1 = cpu_oracle_1thread(mesh, seg)
+        # near-degenerate segments (a crossing within 1e-6 of an edge or an
+        # end, or coplanar), counted by the oracle on a sample of each
+        # workload; the kernels match the oracle on them too
+        res["breakdown"]["neardeg_per_seg"] = neardeg_rate(mesh, seg)
+        if "fwd_bwd" in res:
+            dmesh, dseg, _ = synth.workload_diff()
+            res["fwd_bwd"]["neardeg_per_seg"] = neardeg_rate(dmesh, dseg)
         res["cpu_baseline"] = {"value": round(rate, 5), "unit": UNIT, "cores": thr,
                                "kind": "oracle",
                                "sample": f"first {n} of the 10M segments, CPU BVH build + "
@@ -374,17 +390,49 @@ def run_extras(args, torch, rsi, synth, dev, stream):
             o = bvh.intersect(A, B, "nearest", stream=stream)
             rsi.intersect_backward(V, T, A, B, o["tri"], grad_point=W, stream=stream)
 
+        # the same training step through the public autograd API: an in-place
+        # update of the vertex parameter (as an optimizer makes; it bumps the
+        # tensor's version), then nearest_hit with the reused tree, which
+        # refits it, and the backward pass of loss = sum(w . P)
+        Vp = V.clone().requires_grad_(True)
+        bvh_ag = rsi.BVH(Vp.detach(), T, stream=stream)
+        nudge = [1e-7]
+
+        def fwd_bwd_autograd():
+            with torch.no_grad():
+                Vp.add_(nudge[0])
+            nudge[0] = -nudge[0]
+            P, _, _ = rsi.nearest_hit(Vp, T, A, B, bvh=bvh_ag)
+            (P * W).sum().backward()
+
         for _ in range(3):
             fwd_bwd()
             fwd_bwd_refit()
+            fwd_bwd_autograd()
         ms_fb = timed(fwd_bwd, steps, stream, torch)
         ms_f = timed(lambda: (bvh.build(V, T, stream=stream), fwd()), steps, stream, torch)
         ms_fr = timed(fwd_bwd_refit, steps, stream, torch)
+        refits0 = bvh_ag.refits
+        ms_fa = timed(fwd_bwd_autograd, steps, stream, torch)
+        if bvh_ag.refits - refits0 != steps:
+            raise RuntimeError("nearest_hit did not refit the reused tree every step")
+        st = bvh.intersect(A, B, "nearest", stats=True, stream=stream)["stats"]
         out["fwd_bwd"] = {"workload": "heightfield 257x257 (131,072 tris) x 262,144 near-vertical "
                                       "segments, nearest + adjoint, build included",
                           "value": round(seg.n / (ms_fb * 1e-3) / 1e6, 3), "unit": UNIT,
                           "forward_only": round(seg.n / (ms_f * 1e-3) / 1e6, 3),
-                          "with_refit": round(seg.n / (ms_fr * 1e-3) / 1e6, 3)}
+                          "with_refit": round(seg.n / (ms_fa * 1e-3) / 1e6, 3),
+                          "with_refit_note": "torch autograd step: in-place vertex update, "
+                                             "nearest_hit with the reused tree (refit), "
+                                             "backward of sum(w . P)",
+                          "with_refit_direct": round(seg.n / (ms_fr * 1e-3) / 1e6, 3),
+                          "nearest_breakdown": {
+                              "node_visits_per_seg": round(st["node_visits"] / seg.n, 3),
+                              "tri_tests_per_seg": round(st["tri_tests"] / seg.n, 3),
+                              "fp64_decisions_per_seg": st["fp64_tests"] / seg.n,
+                              "df_refines_per_seg": round(st["df_refines"] / seg.n, 5),
+                              "fp64_values_per_seg": st["fp64_values"] / seg.n}}
+        del bvh_ag, Vp
         del bvh
         # count + nearest on the big sphere
         mesh, seg = synth.workload_sphere()
@@ -400,8 +448,14 @@ def run_extras(args, torch, rsi, synth, dev, stream):
                        torch)
             res[mode] = round(seg.n / (ms * 1e-3) / 1e6, 3)
         ms_b = timed(lambda: bvh.build(V, T, stream=stream), steps, stream, torch)
+        st = bvh.intersect(A, B, "nearest", stats=True, stream=stream)["stats"]
         out["sphere"] = {"workload": "icosphere L8 (1,310,720 tris) x 1M segments in a cube",
-                         "traverse_Msegs": res, "build_ms": round(ms_b, 3), "unit": UNIT}
+                         "traverse_Msegs": res, "build_ms": round(ms_b, 3), "unit": UNIT,
+                         "nearest_breakdown": {
+                             "node_visits_per_seg": round(st["node_visits"] / seg.n, 3),
+                             "tri_tests_per_seg": round(st["tri_tests"] / seg.n, 3),
+                             "df_refines_per_seg": round(st["df_refines"] / seg.n, 5),
+                             "fp64_values_per_seg": st["fp64_values"] / seg.n}}
         del bvh
         # coherent segments: one stack per segment against warp packets
         mesh, seg = synth.workload_raster()

@@ -185,7 +185,16 @@ class BVH:
                                                 C.byref(h)), "rsi_bvh_create")
         self._h = h
         self.T = T
+        self.refits = 0
+        self._vkey = None
         self.build(V, T, stream)
+
+    @staticmethod
+    def _key(V):
+        # storage, in-place version and shape of the vertices the tree holds:
+        # an optimizer step on V (in place) bumps the version, a new tensor
+        # has another storage
+        return (V.data_ptr(), V._version, tuple(V.shape))
 
     def build(self, V, T=None, stream=None):
         """Rebuild from vertices V (and triangles T, same sizes)."""
@@ -198,14 +207,32 @@ class BVH:
             _abi.check(self._lib.rsi_bvh_build(self._h, _vp(V), _vp(T), _stream(stream)),
                        "rsi_bvh_build")
         self.T = T
+        self._tkey = T._version
+        self._vkey = self._key(V)
         return self
 
     def refit(self, V, stream=None):
         """Refit the boxes to moved vertices (same triangles as the last build)."""
         _check_tensor(V, "V", torch.float32)
+        if V.shape[0] != self.nV:
+            raise ValueError("refit: vertex count differs from the handle's")
         with torch.cuda.device(self.device):
             _abi.check(self._lib.rsi_refit(self._h, _vp(V), _vp(self.T), _stream(stream)),
                        "rsi_refit")
+        self._vkey = self._key(V)
+        self.refits += 1
+        return self
+
+    def sync(self, V, T=None, stream=None):
+        """Make the tree describe vertices V (and triangles T): a rebuild when
+        T is not the tensor the tree was built from, a refit (the bottom-up
+        box pass, Sec. 2) when V is another tensor or was changed in place
+        since the last build or refit, nothing otherwise."""
+        if T is not None and (T.data_ptr() != self.T.data_ptr() or T.shape != self.T.shape
+                              or T._version != self._tkey):
+            return self.build(V, T, stream)
+        if self._key(V) != self._vkey:
+            self.refit(V, stream)
         return self
 
     def status(self, stream=None) -> int:
@@ -367,12 +394,17 @@ def intersect_backward(V, T, A, B, tri, grad_point=None, grad_tuv=None, grad_V=N
 class RSIFunction(torch.autograd.Function):
     """Nearest crossing as a differentiable function of (V, A, B): returns
     (point [nR,3], tuv [nR,3], tri [nR]); hit/miss and the triangle are held
-    fixed in the backward pass (rsi_intersect_backward)."""
+    fixed in the backward pass (rsi_intersect_backward).  With a `bvh` passed
+    the tree is reused across calls and kept current: refit when V is
+    another tensor or was changed in place (an optimizer step) since the
+    tree last saw it, rebuilt when T is another tensor (BVH.sync)."""
 
     @staticmethod
     def forward(ctx, V, A, B, T, bvh):
         if bvh is None:
             bvh = BVH(V.detach(), T)
+        else:
+            bvh.sync(V.detach(), T)
         o = bvh.intersect(A.detach(), B.detach(), "nearest")
         ctx.save_for_backward(V.detach(), A.detach(), B.detach(), T, o["tri"])
         ctx.mark_non_differentiable(o["tri"])
@@ -388,7 +420,8 @@ class RSIFunction(torch.autograd.Function):
 
 
 def nearest_hit(V, T, A, B, bvh=None):
-    """Differentiable nearest crossing: (point, tuv, tri)."""
+    """Differentiable nearest crossing: (point, tuv, tri).  Pass a BVH of
+    (V, T) to reuse it across steps: it is refit whenever V has moved."""
     return RSIFunction.apply(V, A, B, T, bvh)
 
 

@@ -10,6 +10,8 @@ import oracle
 import paper_2209_02878_gb300 as rsi
 from paper_2209_02878_gb300 import synth
 
+from _util import assert_close
+
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
 
@@ -121,10 +123,16 @@ def test_adjoint_vs_finite_differences(diff_case):
 
 
 def test_translation_invariance(diff_case):
+    """Moving the mesh and the segments together moves every crossing point
+    with them: the gradients sum to the sum of dL/dP over the hits (per
+    axis).  Each gradient entry is within 1e-5 of its value (relative), so
+    the sum is within 1e-5 of the sum of their magnitudes."""
     _, _, w, ref, got, _ = diff_case
-    total = got["gV"].sum(0) + got["gA"].sum(0) + got["gB"].sum(0)
+    terms = [got["gV"], got["gA"], got["gB"]]
+    total = sum(t.sum(0) for t in terms)
+    mag = sum(np.abs(t).sum(0) for t in terms)
     want = w[ref["tri"] >= 0].astype(np.float64).sum(0)
-    assert np.allclose(total, want, rtol=1e-4, atol=1e-2)
+    assert np.all(np.abs(total - want) <= 1e-5 * mag), (total, want, mag)
 
 
 def test_sharded_backward_sums_to_unsharded(diff_case):
@@ -144,3 +152,40 @@ def test_sharded_backward_sums_to_unsharded(diff_case):
     torch.cuda.synchronize()
     assert rel_l2(acc.cpu().numpy().astype(np.float64), got["gV"]) <= 1e-6
     assert torch.equal(o["tri"], tri)
+
+
+def test_reused_tree_follows_optimizer_steps():
+    """Three SGD steps on the vertices of the differentiable workload with
+    one BVH passed to nearest_hit throughout: each step's forward refits the
+    tree to the moved vertices (an in-place optimizer update bumps V's
+    version), and its outputs and gradients match the oracle on those
+    vertices.  A step moves vertices by up to about a grid cell, so a stale
+    tree would miss crossings."""
+    mesh, seg, w = synth.workload_diff()
+    V = dev(mesh.V).requires_grad_(True)
+    T, A, B, W = dev(mesh.T), dev(seg.A), dev(seg.B), dev(w)
+    bvh = rsi.BVH(V.detach(), T)
+    opt = torch.optim.SGD([V], lr=2e-3)
+    moved = 0.0
+    for step in range(3):
+        Vh = V.detach().cpu().numpy()
+        P, tuv, tri = rsi.nearest_hit(V, T, A, B, bvh=bvh)
+        opt.zero_grad()
+        (P * W).sum().backward()
+        torch.cuda.synchronize()
+        assert bvh.refits == step
+        ref = oracle.CpuBVH(Vh, mesh.T).query(seg.A, seg.B)
+        np.testing.assert_array_equal(tri.cpu().numpy(), ref["tri"], err_msg=f"step {step}")
+        assert_close(P.detach().cpu().numpy(), ref["point"], what=f"step {step} point")
+        assert_close(tuv.detach().cpu().numpy(), ref["tuv"], what=f"step {step} tuv")
+        gV, _, _ = oracle.backward(Vh, mesh.T, seg.A, seg.B, ref["tri"], gP=w.astype(np.float64))
+        g = V.grad.cpu().numpy().astype(np.float64)
+        assert rel_l2(g, gV) <= 1e-5, step
+        nz = np.nonzero(gV.ravel())[0]
+        idx = np.random.default_rng(step).choice(nz, 1000, replace=False)
+        assert elementwise_ok(g.ravel(), gV.ravel(), idx).all(), step
+        before = V.detach().clone()
+        opt.step()
+        moved = max(moved, float((V.detach() - before).abs().max()))
+    assert bvh.refits == 2
+    assert moved > 1e-3, moved
