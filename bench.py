@@ -288,7 +288,7 @@ def run_ours(args):
 
     extras = {}
     if not args.quick:
-        extras = run_extras(args, torch, rsi, synth, dev, stream)
+        extras = run_extras(args, torch, rsi, synth, dev, stream, dist)
 
     peak, peak_kind = measured_peaks()
     algo_bytes = BYTES_PER_SEG_BOOL * n_seg
@@ -360,7 +360,7 @@ def run_ours(args):
         print(json.dumps(res))
 
 
-def run_extras(args, torch, rsi, synth, dev, stream):
+def run_extras(args, torch, rsi, synth, dev, stream, dist=None):
     """fwd+bwd (131k-triangle heightfield, 262k segments), count + nearest
     (1.3M-triangle icosphere, 1M segments), a coherent raster of segments
     (per-segment stacks against warp packets) and the 64-mesh batch, each
@@ -433,6 +433,34 @@ def run_extras(args, torch, rsi, synth, dev, stream):
                               "df_refines_per_seg": round(st["df_refines"] / seg.n, 5),
                               "fp64_values_per_seg": st["fp64_values"] / seg.n}}
         del bvh_ag, Vp
+        # the same step sharded over the ranks (data parallel): each rank
+        # builds the replicated mesh's tree and runs its contiguous shard of
+        # the segments; the vertex gradient is all-reduced (the one
+        # collective; none at one rank)
+        from paper_2209_02878_gb300 import sharding
+        world = dist.get_world_size() if dist else 1
+        bvh_sh = rsi.BVH(V, T, stream=stream)
+
+        def sharded_step():
+            bvh_sh.build(V, T, stream=stream)
+            sharding.nearest_backward_shard(V, T, A, B, grad_point=W, bvh=bvh_sh, stream=stream)
+
+        for _ in range(3):
+            sharded_step()
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        ms_sh = timed(sharded_step, steps, stream, torch)
+        if dist:
+            t_ = torch.tensor([ms_sh], device=dev)
+            dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+            ms_sh = float(t_.item())
+        out["fwd_bwd"]["sharded"] = {
+            "value": round(seg.n / (ms_sh * 1e-3) / 1e6, 3), "unit": UNIT, "ranks": world,
+            "scaling": "strong",
+            "note": "the 262,144 segments split into contiguous per-rank shards, mesh "
+                    "replicated (tree built per rank per step), grad_V all-reduced over ranks"}
+        del bvh_sh
         del bvh
         # count + nearest on the big sphere
         mesh, seg = synth.workload_sphere()

@@ -525,8 +525,8 @@ __device__ __forceinline__ float df_float(dfl a) { return __fadd_rn(a.h, a.l); }
 // exact in double-float); t is returned as a double-float pair so that the
 // point a + t d can be formed without rounding t to FP32 first.  Only used
 // for values, never for decisions.
-static __device__ __noinline__ void mt_df(const float* a3, const float* b3, float4 A, float4 B,
-                                   float4 C, dfl& t, float& u, float& v) {
+__device__ __forceinline__ void mt_df(const float* a3, const float* b3, float4 A, float4 B,
+                                      float4 C, dfl& t, float& u, float& v) {
     dfl d[3], e1[3], e2[3], s0[3];
     const float v0[3] = {A.x, A.y, A.z}, v1[3] = {B.x, B.y, B.z}, v2[3] = {C.x, C.y, C.z};
     for (int k = 0; k < 3; ++k) {

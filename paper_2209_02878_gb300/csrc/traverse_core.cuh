@@ -378,22 +378,31 @@ static __device__ __noinline__ void values64(const float* A, const float* B, int
     o[6] = (float)__dmul_rn(tuv[0], __dsqrt_rn(dd));
 }
 
-// Nearest outputs recomputed in double-float, written to o[0..6] as above;
-// the point from the unrounded double-float t and the exact d = b - a
-// (two-sum), since the FP32 rounding of t times a long |d| can exceed the
-// tolerance.
+// Nearest outputs recomputed in double-float, written to o[0..6] as above.
+// The point: for |d| < 64 fma(t, fl(d), a) with t rounded to FP32 is off by
+// at most |d| (2u t) + u max(1, |P|) < 0.8e-5 (the rounding of t and of
+// fl(b - a), u = 2^-24); longer segments form it from the unrounded
+// double-float t and the exact d = b - a (two-sum).
 static __device__ __noinline__ void values_df(const float* a3, const float* b3, float4 v0,
                                               float4 v1, float4 v2, float* o) {
     dfl t;
-    mt_df(a3, b3, v0, v1, v2, t, o[1], o[2]);
-    o[0] = df_float(t);
-    float dd = 0.f;
-    for (int k = 0; k < 3; ++k) {
-        const dfl d = df_two_sum(b3[k], -a3[k]);
-        o[3 + k] = df_float(df_add({a3[k], 0.f}, df_mul(t, d)));
-        dd = fmaf(d.h, d.h, dd);
+    float u, v;
+    mt_df(a3, b3, v0, v1, v2, t, u, v);
+    const float tf = df_float(t);
+    const float dx = b3[0] - a3[0], dy = b3[1] - a3[1], dz = b3[2] - a3[2];
+    const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (dd < 4096.f) {
+        o[3] = fmaf(tf, dx, a3[0]);
+        o[4] = fmaf(tf, dy, a3[1]);
+        o[5] = fmaf(tf, dz, a3[2]);
+    } else {
+        for (int k = 0; k < 3; ++k)
+            o[3 + k] = df_float(df_add({a3[k], 0.f}, df_mul(t, df_two_sum(b3[k], -a3[k]))));
     }
-    o[6] = o[0] * sqrtf(dd);
+    o[0] = tf;
+    o[1] = u;
+    o[2] = v;
+    o[6] = tf * sqrtf(dd);
 }
 
 // Nearest outputs.  (t, u, v) keep their FP32 values when a rigorous bound

@@ -50,6 +50,69 @@ def _worker(rank, world, port, out_dir):
         dist.destroy_process_group()
 
 
+def _step_worker(rank, world, port, out_dir):
+    """The product helper nearest_backward_shard on a gloo rank, its two
+    compute steps supplied by the FP64 oracle (no GPU here)."""
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        mesh, seg, w = _case()
+        A, B, W = (torch.from_numpy(x) for x in (seg.A, seg.B, w))
+        gt = torch.from_numpy(np.random.default_rng(7).normal(size=(seg.n, 3)).astype(np.float32))
+
+        def forward(a, b):
+            return {"tri": oracle.brute(mesh.V, mesh.T, a.numpy(), b.numpy(), threads=1)["tri"]}
+
+        def backward(tri, a, b, gp, g_tuv):
+            gV, gA, gB = oracle.backward(mesh.V, mesh.T, a.numpy(), b.numpy(), tri,
+                                         gP=gp.numpy().astype(np.float64),
+                                         gtuv=g_tuv.numpy().astype(np.float64))
+            return torch.from_numpy(gV), torch.from_numpy(gA), torch.from_numpy(gB)
+
+        r = sharding.nearest_backward_shard(None, None, A, B, grad_point=W, grad_tuv=gt,
+                                            forward=forward, backward=backward)
+        lo, hi = r["range"]
+        parts = [None] * world
+        dist.all_gather_object(parts, (lo, hi, r["out"]["tri"], r["grad_A"].numpy(),
+                                       r["grad_B"].numpy()))
+        if rank == 0:
+            np.save(os.path.join(out_dir, "step_gV.npy"), r["grad_V"].numpy())
+            parts.sort(key=lambda p: p[0])
+            assert parts[0][0] == 0 and parts[-1][1] == seg.n
+            for k in range(len(parts) - 1):
+                assert parts[k][1] == parts[k + 1][0]
+            np.save(os.path.join(out_dir, "step_tri.npy"), np.concatenate([p[2] for p in parts]))
+            np.save(os.path.join(out_dir, "step_gA.npy"), np.concatenate([p[3] for p in parts]))
+            np.save(os.path.join(out_dir, "step_gB.npy"), np.concatenate([p[4] for p in parts]))
+        else:
+            # every rank holds the summed vertex gradient
+            np.save(os.path.join(out_dir, f"step_gV_{rank}.npy"), r["grad_V"].numpy())
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_nearest_backward_step(tmp_path, orc):
+    """nearest_backward_shard on two gloo ranks: the shards tile the
+    segments, the gathered ids and segment gradients equal the unsharded
+    ones, and every rank ends with the unsharded vertex gradient."""
+    world = 2
+    mp.start_processes(_step_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    mesh, seg, w = _case()
+    gt = np.random.default_rng(7).normal(size=(seg.n, 3)).astype(np.float32)
+    full = orc.brute(mesh.V, mesh.T, seg.A, seg.B)
+    np.testing.assert_array_equal(np.load(tmp_path / "step_tri.npy"), full["tri"])
+    gV, gA, gB = orc.backward(mesh.V, mesh.T, seg.A, seg.B, full["tri"],
+                              gP=w.astype(np.float64), gtuv=gt.astype(np.float64))
+    for name, ref in (("step_gV.npy", gV), ("step_gV_1.npy", gV), ("step_gA.npy", gA),
+                      ("step_gB.npy", gB)):
+        np.testing.assert_allclose(np.load(tmp_path / name), ref, rtol=1e-12, atol=1e-12,
+                                   err_msg=name)
+
+
 def test_two_rank_gloo_sharding(tmp_path, orc):
     world = 2
     mp.start_processes(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world,

@@ -184,10 +184,15 @@ def df_outputs(a, b, v0, v1, v2, pair=False):
         if pair:
             return t
         u, v = (_div(x, det, r) for x in (dp(s0, p), dp(d, q)))
-        P = np.stack([sum(_add((a[:, k], np.zeros_like(a[:, k])), _mul(t, d[k])))
-                      for k in range(3)], axis=1)
         tf = t[0] + t[1]
-        dd = (d[0][0] * d[0][0] + d[1][0] * d[1][0]) + d[2][0] * d[2][0]
+        dd = fmaf(d[0][0], d[0][0], fmaf(d[1][0], d[1][0], d[2][0] * d[2][0]))
+        # |d| < 64: fma(t, fl(d), a) with the rounded t; longer: from the
+        # unrounded t and the exact d
+        P32 = np.stack([(tf.astype(np.float64) * d[k][0].astype(np.float64)
+                         + a[:, k].astype(np.float64)).astype(F) for k in range(3)], axis=1)
+        Pdf = np.stack([sum(_add((a[:, k], np.zeros_like(a[:, k])), _mul(t, d[k])))
+                        for k in range(3)], axis=1)
+        P = np.where((dd < F(4096))[:, None], P32, Pdf)
         return tf, u[0] + u[1], v[0] + v[1], P, tf * np.sqrt(dd)
 
 
