@@ -409,8 +409,24 @@ def run_extras(args, torch, rsi, synth, dev, stream, dist=None):
             fwd_bwd()
             fwd_bwd_refit()
             fwd_bwd_autograd()
-        ms_fb = timed(fwd_bwd, steps, stream, torch)
-        ms_f = timed(lambda: (bvh.build(V, T, stream=stream), fwd()), steps, stream, torch)
+        ms_fb_eager = timed(fwd_bwd, steps, stream, torch)
+        # the same step captured once as a CUDA graph and replayed, as a
+        # training loop with static shapes would run it (build, traversal,
+        # adjoint and their allocations become graph nodes: no per-launch
+        # host work)
+        g_fb = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_fb, stream=stream):
+            fwd_bwd()
+        g_fb.replay()
+        stream.synchronize()
+        ms_fb = timed(g_fb.replay, steps, stream, torch)
+        g_f = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_f, stream=stream):
+            bvh.build(V, T, stream=stream)
+            fwd()
+        g_f.replay()
+        stream.synchronize()
+        ms_f = timed(g_f.replay, steps, stream, torch)
         ms_fr = timed(fwd_bwd_refit, steps, stream, torch)
         refits0 = bvh_ag.refits
         ms_fa = timed(fwd_bwd_autograd, steps, stream, torch)
@@ -420,7 +436,10 @@ def run_extras(args, torch, rsi, synth, dev, stream, dist=None):
         out["fwd_bwd"] = {"workload": "heightfield 257x257 (131,072 tris) x 262,144 near-vertical "
                                       "segments, nearest + adjoint, build included",
                           "value": round(seg.n / (ms_fb * 1e-3) / 1e6, 3), "unit": UNIT,
+                          "graph": True,
+                          "eager": round(seg.n / (ms_fb_eager * 1e-3) / 1e6, 3),
                           "forward_only": round(seg.n / (ms_f * 1e-3) / 1e6, 3),
+                          "forward_only_note": "build + nearest, as a graph",
                           "with_refit": round(seg.n / (ms_fa * 1e-3) / 1e6, 3),
                           "with_refit_note": "torch autograd step: in-place vertex update, "
                                              "nearest_hit with the reused tree (refit), "
