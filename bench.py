@@ -39,7 +39,8 @@ BYTES_PER_SEG_COUNT = 28
 # dram__bytes_read.sum + dram__bytes_write.sum and warp instructions of one
 # k_trace<BOOL> launch on this workload, from an ncu capture of the traversal
 # built from sources hashing to `sha`; reported as null once they differ
-TRAFFIC = {"sha": "53170cf025ef2a14", "bytes": 258_624_768, "warp_inst": 961_191_339}
+TRAFFIC = {"sha": "53170cf025ef2a14", "bytes": 258_624_768, "warp_inst": 961_191_339,
+           "l2_hit_pct": 81.6, "l1_hit_pct": 68.4}
 # peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per cycle at
 # the maximum SM clock (2,070 MHz)
 ISSUE_PEAK = 152 * 4 * 2.070e9
@@ -247,10 +248,14 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
-            # the sampler runs from before the warm-up repeats to after the timed region
-            for _ in range(3):
-                step()
-            stream.synchronize()
+            # the sampler runs from before the warm-up repeats to after the
+            # timed region; about 0.3 s of untimed steps first, so that it
+            # sees the clocks under this load more than a couple of times
+            t_end = time.perf_counter() + 0.3
+            while time.perf_counter() < t_end:
+                for _ in range(20):
+                    step()
+                stream.synchronize()
             ms_step = timed(step, args.steps, stream, torch)
             torch.cuda.synchronize()
         if dist:
@@ -316,6 +321,8 @@ def run_ours(args):
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 5),
                      "peak_kind": peak_kind,
                      "traffic": TRAFFIC["bytes"] if traversal_sha() == TRAFFIC["sha"] else None,
+                     "l2_hit_pct": TRAFFIC["l2_hit_pct"] if traversal_sha() == TRAFFIC["sha"] else None,
+                     "l1_hit_pct": TRAFFIC["l1_hit_pct"] if traversal_sha() == TRAFFIC["sha"] else None,
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "kernel_ms": round(ms_trav, 4)},
         "issue_roofline": ({"bound": "issue", "kernel": "k_trace<BOOL>",

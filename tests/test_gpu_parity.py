@@ -385,6 +385,39 @@ def test_sphere_scale_count_nearest_sampled():
     assert cnt.max() >= 4
 
 
+def test_host_calls_alternate_streams_growing(small):
+    """Host-buffer calls on one handle alternating between two streams, each
+    ordered after the previous call by an event (the handle's rule), with
+    growing segment counts so that the staging is reallocated between calls
+    (freed on the current call's stream, which follows every earlier use):
+    every result matches the oracle, in every mode and host path."""
+    mesh, seg, ref = small
+    V, T = dev(mesh.V), dev(mesh.T)
+    bvh = rsi.BVH(V, T)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    calls = []
+    prev = None
+    for k, n in enumerate([500, 1500, 3000, 6007, 10000]):
+        s = streams[k % 2]
+        if prev is not None:
+            s.wait_event(prev)
+        A = torch.from_numpy(seg.A[:n]).pin_memory()
+        B = torch.from_numpy(seg.B[:n]).pin_memory()
+        mode = ("bool", "count", "nearest")[k % 3]
+        # the streamed BOOL path, the in-place path and the staged path (pageable)
+        if k == 3:
+            A, B = torch.from_numpy(seg.A[:n].copy()), torch.from_numpy(seg.B[:n].copy())
+        calls.append((n, mode, bvh.intersect_host(A, B, mode, chunk=1024, stream=s), A, B))
+        prev = torch.cuda.Event()
+        prev.record(s)
+    for s in streams:
+        s.synchronize()
+    for n, mode, o, _, _ in calls:
+        key = {"bool": "flag", "count": "count", "nearest": "tri"}[mode]
+        np.testing.assert_array_equal(o[key].numpy(), ref[key][:n], err_msg=f"{mode} n={n}")
+    assert bvh.status(streams[0]) == 0
+
+
 def test_host_calls_back_to_back(small):
     """Streamed BOOL calls, in-place COUNT / NEAREST calls and rebuilds
     queued on one stream without synchronising in between, with inputs of
