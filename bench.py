@@ -280,8 +280,17 @@ def run_ours(args):
         hB = torch.from_numpy(seg.B).pin_memory()
         hout = {"flag": torch.empty(n_seg, dtype=torch.uint8).pin_memory()}
 
+        # the build replayed from a CUDA graph, as in the device step (the
+        # host call itself runs eagerly: it stages, flags and copies back)
+        build_step = bvh.build
+        if not args.no_graph:
+            g_build = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g_build, stream=stream):
+                bvh.build(V, T, stream=stream)
+            build_step = lambda V_, T_, stream=None: g_build.replay()  # noqa: E731
+
         def e2e_step():
-            bvh.build(V, T, stream=stream)
+            build_step(V, T, stream=stream)
             bvh.intersect_host(hA, hB, "bool", out=hout, stream=stream)
 
         for _ in range(2):

@@ -189,3 +189,41 @@ def test_reused_tree_follows_optimizer_steps():
         moved = max(moved, float((V.detach() - before).abs().max()))
     assert bvh.refits == 2
     assert moved > 1e-3, moved
+
+
+def test_sharded_step_helper_at_one_rank(diff_case):
+    """sharding.nearest_backward_shard on its default CUDA path with no
+    process group (one rank, the whole range, no collective) gives the
+    unsharded forward and gradients."""
+    from paper_2209_02878_gb300 import sharding
+    mesh, seg, w, ref, got, _ = diff_case
+    V, T = dev(mesh.V), dev(mesh.T)
+    r = sharding.nearest_backward_shard(V, T, dev(seg.A), dev(seg.B), grad_point=dev(w))
+    torch.cuda.synchronize()
+    assert r["range"] == (0, seg.n)
+    np.testing.assert_array_equal(r["out"]["tri"].cpu().numpy(), ref["tri"])
+    for key, g in (("gV", r["grad_V"]), ("gA", r["grad_A"]), ("gB", r["grad_B"])):
+        assert rel_l2(g.cpu().numpy().astype(np.float64), got[key]) <= 1e-6, key
+
+
+def test_reused_tree_rebuilds_for_new_triangles():
+    """BVH.sync with another triangle tensor rebuilds the tree (the
+    topology changed), and results follow the new triangles."""
+    mesh, seg = synth.workload_small_bool(n_seg=3000)
+    V, A, B = dev(mesh.V), dev(seg.A), dev(seg.B)
+    T1 = dev(mesh.T)
+    T2 = dev(mesh.T[::-1].copy())          # the same triangles in reverse order
+    bvh = rsi.BVH(V, T1)
+    P1, _, tri1 = rsi.nearest_hit(V, T1, A, B, bvh=bvh)
+    P2, _, tri2 = rsi.nearest_hit(V, T2, A, B, bvh=bvh)
+    torch.cuda.synchronize()
+    assert bvh.T is T2 and bvh.refits == 0
+    n = mesh.n_tri
+    t1, t2 = tri1.cpu().numpy(), tri2.cpu().numpy()
+    hit = t1 >= 0
+    # the same crossings, triangle ids mapped through the reversal (except
+    # ties on t, which go to the lower index of each numbering)
+    ref2 = oracle.brute(mesh.V, mesh.T[::-1].copy(), seg.A, seg.B)
+    np.testing.assert_array_equal(t2, ref2["tri"])
+    assert np.array_equal(t2 >= 0, hit)
+    assert (n - 1 - t2[hit] == t1[hit]).mean() > 0.99
