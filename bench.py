@@ -444,6 +444,12 @@ def run_extras(args, torch, rsi, synth, dev, stream, dist=None):
         stream.synchronize()
         ms_f = timed(g_f.replay, steps, stream, torch)
         ms_fr = timed(fwd_bwd_refit, steps, stream, torch)
+        g_fr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_fr, stream=stream):
+            fwd_bwd_refit()
+        g_fr.replay()
+        stream.synchronize()
+        ms_frg = timed(g_fr.replay, steps, stream, torch)
         refits0 = bvh_ag.refits
         ms_fa = timed(fwd_bwd_autograd, steps, stream, torch)
         if bvh_ag.refits - refits0 != steps:
@@ -461,6 +467,7 @@ def run_extras(args, torch, rsi, synth, dev, stream, dist=None):
                                              "nearest_hit with the reused tree (refit), "
                                              "backward of sum(w . P)",
                           "with_refit_direct": round(seg.n / (ms_fr * 1e-3) / 1e6, 3),
+                          "with_refit_graph": round(seg.n / (ms_frg * 1e-3) / 1e6, 3),
                           "nearest_breakdown": {
                               "node_visits_per_seg": round(st["node_visits"] / seg.n, 3),
                               "tri_tests_per_seg": round(st["tri_tests"] / seg.n, 3),
