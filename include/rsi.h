@@ -319,7 +319,7 @@ rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR
  * When hA and hB both lie in page-locked memory the device can address
  * (cudaHostAlloc / cudaHostRegister, unified addressing): in BOOL mode one
  * persistent traversal starts at once while the copy engine streams the
- * segments into device staging in chunks of `chunk` (0 -> 2^19, rounded up
+ * segments into device staging in chunks of `chunk` (0 -> 2^20, rounded up
  * to 32) and flags each chunk as it lands, the warps waiting (bounded:
  * RSI_ERR_TIMEOUT in the handle's status) for the chunks they take (two
  * staging slots used in turn, 25 B per segment each); in COUNT / NEAREST

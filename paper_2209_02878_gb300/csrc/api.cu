@@ -31,7 +31,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr int kDefaultBlock = 128;
 constexpr int64_t kHostChunk = (int64_t)1 << 21;  // segments per pipeline chunk
 constexpr int64_t kHostChunkInPlace = (int64_t)1 << 24;  // the same, BOOL read in place
-constexpr int64_t kStreamChunk = (int64_t)1 << 19;  // segments per streamed copy (BOOL)
+constexpr int64_t kStreamChunk = (int64_t)1 << 20;  // segments per streamed copy (BOOL)
 constexpr int64_t kStreamMaxChunks = 256;
 constexpr int64_t kStreamMax = (int64_t)1 << 28;      // larger inputs take the chunked path
 
