@@ -378,39 +378,23 @@ static __device__ __noinline__ void values64(const float* A, const float* B, int
     o[6] = (float)__dmul_rn(tuv[0], __dsqrt_rn(dd));
 }
 
-// Nearest outputs recomputed in double-float, written to o[0..6] as above.
-// The point: for |d| < 64 fma(t, fl(d), a) with t rounded to FP32 is off by
-// at most |d| (2u t) + u max(1, |P|) < 0.8e-5 (the rounding of t and of
-// fl(b - a), u = 2^-24); longer segments form it from the unrounded
-// double-float t and the exact d = b - a (two-sum).
+// (t, u, v) recomputed in double-float and rounded to FP32, written to
+// tuv[0..2] (out of line; returns through the caller's local array).
 static __device__ __noinline__ void values_df(const float* a3, const float* b3, float4 v0,
-                                              float4 v1, float4 v2, float* o) {
+                                              float4 v1, float4 v2, float* tuv) {
     dfl t;
-    float u, v;
-    mt_df(a3, b3, v0, v1, v2, t, u, v);
-    const float tf = df_float(t);
-    const float dx = b3[0] - a3[0], dy = b3[1] - a3[1], dz = b3[2] - a3[2];
-    const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (dd < 4096.f) {
-        o[3] = fmaf(tf, dx, a3[0]);
-        o[4] = fmaf(tf, dy, a3[1]);
-        o[5] = fmaf(tf, dz, a3[2]);
-    } else {
-        for (int k = 0; k < 3; ++k)
-            o[3 + k] = df_float(df_add({a3[k], 0.f}, df_mul(t, df_two_sum(b3[k], -a3[k]))));
-    }
-    o[0] = tf;
-    o[1] = u;
-    o[2] = v;
-    o[6] = tf * sqrtf(dd);
+    mt_df(a3, b3, v0, v1, v2, t, tuv[1], tuv[2]);
+    tuv[0] = df_float(t);
 }
 
 // Nearest outputs.  (t, u, v) keep their FP32 values when a rigorous bound
 // (first the filter's, then a tighter one for this triangle) shows them, and
 // the point, within the tolerance.  Otherwise they are recomputed: in
-// double-float while the tight bound still keeps det away from zero and the
-// double-float error of t (below 2^-20 of that bound; measured: 2e-8), times
-// |d| for the point, stays within half the tolerance; with the FP64
+// double-float (t, u, v rounded to FP32, the point fma(t, fl(d), a)) while
+// the tight bound still keeps det away from zero, the double-float error of
+// t (below 2^-20 of that bound; measured: 2e-8) times |d| stays within half
+// the tolerance, and |d| < 64 (so that the rounding of t and of fl(b - a),
+// |d| 2u t, plus the point's own rounding stays below 0.8e-5); with the FP64
 // definition where it does not (a crossing at a grazing angle, or a long
 // segment), or where the segment's direction is outside the FP32 filter's
 // range.
@@ -446,7 +430,7 @@ __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, con
             u = u2;
             v = v2;
             refine = false;
-        } else if (!(et < INFINITY && dlen * et <= 4.f && euv <= 4.f)) {
+        } else if (!(et < INFINITY && dlen * et <= 4.f && euv <= 4.f) || dlen >= 64.f) {
             exact = true;
         }
     }
@@ -468,17 +452,12 @@ __device__ __forceinline__ void nearest_values(const Seg& s, const float* A, con
         if (STATS) ++st.refines;
         const float a3[3] = {s.ax(), s.ay(), s.az()};
         const float b3[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
-        float o[7];
+        float tuv[3];
         values_df(a3, b3, ld4(tris + 3 * (int64_t)p), ld4(tris + 3 * (int64_t)p + 1),
-                  ld4(tris + 3 * (int64_t)p + 2), o);
-        t = o[0];
-        u = o[1];
-        v = o[2];
-        P[0] = o[3];
-        P[1] = o[4];
-        P[2] = o[5];
-        dist = o[6];
-        return;
+                  ld4(tris + 3 * (int64_t)p + 2), tuv);
+        t = tuv[0];
+        u = tuv[1];
+        v = tuv[2];
     }
     P[0] = fmaf(t, s.dx, s.ax());
     P[1] = fmaf(t, s.dy, s.ay());

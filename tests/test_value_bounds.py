@@ -12,9 +12,9 @@ on the adversarial inputs of tests/_adversarial.py:
   keep the determinant away from zero;
 - the kernels' whole rule for the nearest outputs (`nearest_values` in
   csrc/traverse_core.cuh: FP32 values accepted under the bound-derived
-  thresholds with the point fma(t, fl(d), a); double-float values and a
-  point from the unrounded t where the bound still separates det from zero
-  and |d| times the bound stays small; the FP64 definition otherwise) must
+  thresholds with the point fma(t, fl(d), a); double-float (t, u, v) with
+  the same point where the bound still separates det from zero, |d| times
+  the bound stays small and |d| < 64; the FP64 definition otherwise) must
   give every output of every hit within the 1e-5 tolerance, and the
   double-float t must stay far below 2^-20 of the FP32 bound, the margin
   that rule takes;
@@ -161,8 +161,9 @@ def df_t(a, b, v0, v1, v2):
 
 
 def df_outputs(a, b, v0, v1, v2, pair=False):
-    """(t, u, v, P, dist) as the double-float recomputation forms them: the
-    point from the double-float t and the exact d = b - a (two-sum)."""
+    """(t, u, v, P, dist) as the double-float recomputation forms them:
+    (t, u, v) rounded to FP32, the point fma(t, fl(d), a) (the rule sends
+    segments with |d| >= 64 to FP64 instead)."""
     with np.errstate(all="ignore"):
         d = [_two_sum(b[:, k], -a[:, k]) for k in range(3)]
         e1 = [_two_sum(v1[:, k], -v0[:, k]) for k in range(3)]
@@ -186,13 +187,8 @@ def df_outputs(a, b, v0, v1, v2, pair=False):
         u, v = (_div(x, det, r) for x in (dp(s0, p), dp(d, q)))
         tf = t[0] + t[1]
         dd = fmaf(d[0][0], d[0][0], fmaf(d[1][0], d[1][0], d[2][0] * d[2][0]))
-        # |d| < 64: fma(t, fl(d), a) with the rounded t; longer: from the
-        # unrounded t and the exact d
-        P32 = np.stack([(tf.astype(np.float64) * d[k][0].astype(np.float64)
-                         + a[:, k].astype(np.float64)).astype(F) for k in range(3)], axis=1)
-        Pdf = np.stack([sum(_add((a[:, k], np.zeros_like(a[:, k])), _mul(t, d[k])))
-                        for k in range(3)], axis=1)
-        P = np.where((dd < F(4096))[:, None], P32, Pdf)
+        P = np.stack([(tf.astype(np.float64) * d[k][0].astype(np.float64)
+                       + a[:, k].astype(np.float64)).astype(F) for k in range(3)], axis=1)
         return tf, u[0] + u[1], v[0] + v[1], P, tf * np.sqrt(dd)
 
 
@@ -222,7 +218,7 @@ def nearest_outputs(a, b, v0, v1, v2):
         dlen = np.sqrt(fmaf(d[:, 0], d[:, 0], fmaf(d[:, 1], d[:, 1], d[:, 2] * d[:, 2]))) * F(1.0001)
         thresh = F(0.95) * ((F(1e-5) - F(U)) / np.maximum(F(1), dlen) - F(U))
         accept = (et <= thresh) & (euv <= F(0.95e-5))
-        exact = ~np.isfinite(et) | (dlen * et > F(4)) | (euv > F(4))
+        exact = ~np.isfinite(et) | (dlen * et > F(4)) | (euv > F(4)) | (dlen >= F(64))
         path = np.where(accept, 0, np.where(exact, 2, 1))
         P32 = (t32.astype(np.float64)[:, None] * d.astype(np.float64)
                + a.astype(np.float64)).astype(F)                    # fmaf(t, fl(d), a)
