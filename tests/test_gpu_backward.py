@@ -227,3 +227,45 @@ def test_reused_tree_rebuilds_for_new_triangles():
     np.testing.assert_array_equal(t2, ref2["tri"])
     assert np.array_equal(t2 >= 0, hit)
     assert (n - 1 - t2[hit] == t1[hit]).mean() > 0.99
+
+
+def test_autograd_step_replays_from_a_cuda_graph():
+    """The whole training step -- an in-place vertex update, nearest_hit with
+    a reused tree (which refits it), the backward pass -- captured once with
+    torch.cuda.graph and replayed: after every replay the outputs and the
+    vertex gradient match the oracle on the moved vertices (the refit is in
+    the graph; nothing of the step needs the host)."""
+    rng = np.random.default_rng(17)
+    mesh = synth.heightfield(65, rng)
+    n = 20000
+    xy = rng.uniform(0.02, 0.98, size=(n, 2))
+    A_np = np.c_[xy, -np.ones(n)].astype(np.float32)
+    B_np = np.c_[xy + rng.normal(0.0, 0.02, size=(n, 2)), np.ones(n)].astype(np.float32)
+    w = rng.normal(size=(n, 3)).astype(np.float32)
+    step_np = (rng.normal(size=mesh.V.shape) * 2e-3).astype(np.float32)
+    V = dev(mesh.V).requires_grad_(True)
+    T, A, B, W, D = dev(mesh.T), dev(A_np), dev(B_np), dev(w), dev(step_np)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        bvh = rsi.BVH(V.detach(), T, stream=s)
+        P, _, _ = rsi.nearest_hit(V, T, A, B, bvh=bvh)      # warm-up, eager
+        (P * W).sum().backward()
+        s.synchronize()
+        V.grad = None
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            with torch.no_grad():
+                V.add_(D)
+            P, tuv, tri = rsi.nearest_hit(V, T, A, B, bvh=bvh)
+            (P * W).sum().backward()
+    assert bvh.refits == 1                                   # captured with the step
+    for k in range(3):
+        g.replay()
+        torch.cuda.synchronize()
+        Vh = V.detach().cpu().numpy()
+        np.testing.assert_allclose(Vh, mesh.V + (k + 1) * step_np, rtol=0, atol=1e-5)
+        ref = oracle.brute(Vh, mesh.T, A_np, B_np)
+        np.testing.assert_array_equal(tri.cpu().numpy(), ref["tri"], err_msg=f"replay {k}")
+        assert_close(P.detach().cpu().numpy(), ref["point"], what=f"replay {k} point")
+        gV, _, _ = oracle.backward(Vh, mesh.T, A_np, B_np, ref["tri"], gP=w.astype(np.float64))
+        assert rel_l2(V.grad.cpu().numpy().astype(np.float64), gV) <= 1e-5, k
