@@ -60,8 +60,10 @@ size_t carve(TreeBufs& tb, int64_t N, int M, int nblk, char* base) {
     tb.rootbox = (float4*)take(16 * 2 * (size_t)M);
     tb.child = (int32_t*)take(4 * 2 * n1);
     tb.range = (int32_t*)take(4 * 2 * n1);
-    tb.parent = (int32_t*)take(4 * 2 * n1);
-    tb.flag = (int32_t*)take(4 * n1);
+    tb.span = (int4*)take(16 * n1);
+    tb.nspan = (int32_t*)take(4);
+    tb.pre = (float4*)take(16 * 2 * n1);
+    tb.suf = (float4*)take(16 * 2 * n1);
     tb.nbox = (float4*)take(16 * 2 * n1);
     tb.lbox = (float4*)take(16 * 2 * n1);
     tb.nodes = (float4*)take(16 * 4 * n1);

@@ -9,17 +9,24 @@
 //   a4  k_karras            : binary radix tree over the distinct keys
 //                             code << 32 | sorted position (Karras 2012, as
 //                             cited in Sec. 2), one thread per internal node
-//   a5  k_climb             : bottom-up boxes, one thread per leaf, the
-//                             second child to arrive at a node merges (the
-//                             per-node `atomic` of Sec. 3.1); writes the
-//                             64-byte traversal nodes and the triangles in
-//                             leaf order; optional leaf collapse
+//   a5  k_boxes_local       : boxes (the bottom-up pass of Sec. 3.1): one
+//                             block per kBoxBlock sorted leaves writes the
+//                             triangles in leaf order, the leaf boxes, a
+//                             shared-memory sparse table of them, and from
+//                             it every node whose leaf range lies inside
+//                             the block, and prefix / suffix unions
+//       k_boxes_span        : the nodes whose leaf range crosses a block
+//                             boundary, from those unions; both write the
+//                             64-byte traversal nodes, with the optional
+//                             leaf collapse
 //       k_treelet           : breadth-first copy of the top levels
 //
 // All kernels work on a concatenation of M meshes (M = 1 for a single
 // handle), so a batch of meshes builds with the same number of launches.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "rsi_build.h"
 #include "rsi_internal.cuh"
@@ -29,19 +36,6 @@ namespace rsi {
 
 __device__ __forceinline__ void latch(int32_t* status, int code) {
     atomicCAS(status, 0, code);
-}
-
-// atomicAdd with acquire-release semantics at device scope (no separate
-// fences): writes before it are visible to the thread that later reads the
-// value it produced, and writes made visible by earlier releases are seen
-// after it.
-__device__ __forceinline__ int atomic_add_acq_rel(int32_t* p, int v) {
-    int old;
-    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;"
-                 : "=r"(old)
-                 : "l"(p), "r"(v)
-                 : "memory");
-    return old;
 }
 
 // Loads triangle j of mesh md; an index outside [0, nV) latches
@@ -187,14 +181,8 @@ __global__ void k_karras(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ 
     if (g >= tb.N) return;
     const MeshDesc md = mesh_of(ma, (int)(keys[g] >> 32));
     const int off = md.off, n = md.n, i = g - off, N = tb.N;
-    tb.flag[g] = 0;
-    if (i == n - 1) {  // root slot of this mesh
-        if (n == 1)
-            tb.parent[N + g] = g;
-        else
-            tb.parent[off] = g;
-        return;
-    }
+    if (g == 0) *tb.nspan = 0;  // the box pass lists the slots that span its blocks
+    if (i == n - 1) return;  // root slot of this mesh
     const int d = kdelta(keys, off, n, i, i + 1) > kdelta(keys, off, n, i, i - 1) ? 1 : -1;
     const int dmin = kdelta(keys, off, n, i, i - d);
     int64_t lmax = 2;  // stops once i + lmax d leaves [0, n)
@@ -218,14 +206,6 @@ __global__ void k_karras(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ 
     tb.child[2 * g + 1] = right;
     tb.range[2 * g] = off + lo;
     tb.range[2 * g + 1] = off + hi;
-    if (left < 0)
-        tb.parent[N + off + gam] = g;
-    else
-        tb.parent[off + gam] = g;
-    if (right < 0)
-        tb.parent[N + off + gam + 1] = g;
-    else
-        tb.parent[off + gam + 1] = g;
 }
 
 // ---------------------------------------------------------------- a5
@@ -316,102 +296,300 @@ __device__ __forceinline__ void write_node4(const float4* __restrict__ nodes, fl
     __stcg(d + 7, make_float4(i2f(o[0].cnt), i2f(o[1].cnt), i2f(o[2].cnt), i2f(o[3].cnt)));
 }
 
-__global__ void k_climb(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ keys,
-                        const uint32_t* __restrict__ vals) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= tb.N) return;
-    const MeshDesc md = mesh_of(ma, (int)(keys[g] >> 32));
-    const int off = md.off, n = md.n, N = tb.N, L = tb.leaf_size;
-    const int root_slot = off + n - 1;
-    const int j = (int)vals[g] - off;
-    float3 a, b, c;
-    const bool ok = tri_vertices(md, j, tb.status, a, b, c);
-    if (!ok) a = b = c = make_float3(0.f, 0.f, 0.f);  // never hits (zero edges)
-    tb.tris[3 * (int64_t)g + 0] = make_float4(a.x, a.y, a.z, i2f(j));
-    tb.tris[3 * (int64_t)g + 1] = make_float4(b.x, b.y, b.z, 0.f);
-    tb.tris[3 * (int64_t)g + 2] = make_float4(c.x, c.y, c.z, 0.f);
-    float4 lo, hi;
-    if (ok) {
-        lo = make_float4(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
-                         fminf(fminf(a.z, b.z), c.z), 0.f);
-        hi = make_float4(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
-                         fmaxf(fmaxf(a.z, b.z), c.z), 0.f);
-    } else {
-        lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-        hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+// Merges box (lo, hi) into (l, h).
+__device__ __forceinline__ void merge_box(float l[3], float h[3], float4 lo, float4 hi) {
+    l[0] = fminf(l[0], lo.x);
+    l[1] = fminf(l[1], lo.y);
+    l[2] = fminf(l[2], lo.z);
+    h[0] = fmaxf(h[0], hi.x);
+    h[1] = fmaxf(h[1], hi.y);
+    h[2] = fmaxf(h[2], hi.z);
+}
+
+__device__ __forceinline__ float4 f4(const float v[3]) { return make_float4(v[0], v[1], v[2], 0.f); }
+
+// Traversal record of internal slot `node` from its two children's boxes and
+// leaf ranges (children of at most leaf_size triangles become leaf ranges);
+// also the slot's own box, and the mesh's root slot when `node` is the Karras
+// root.
+__device__ __forceinline__ void finish_node(const TreeBufs& tb, const MeshDesc& md, int m, int node,
+                                            int2 cc, const float l0[3], const float h0[3],
+                                            int f0, int z0, const float l1[3], const float h1[3],
+                                            int f1, int z1) {
+    const int L = tb.leaf_size;
+    const int ref0 = z0 <= L ? f0 : cc.x, cnt0 = z0 <= L ? z0 : 0;
+    const int ref1 = z1 <= L ? f1 : cc.y, cnt1 = z1 <= L ? z1 : 0;
+    float ul[3] = {l0[0], l0[1], l0[2]}, uh[3] = {h0[0], h0[1], h0[2]};
+    merge_box(ul, uh, f4(l1), f4(h1));
+    __stcg(tb.nbox + 2 * (int64_t)node, f4(ul));
+    __stcg(tb.nbox + 2 * (int64_t)node + 1, f4(uh));
+    write_node(tb.nodes, node, f4(l0), f4(h0), ref0, cnt0, f4(l1), f4(h1), ref1, cnt1);
+    if (node == md.off) {  // Karras root: fill the root slot
+        const int root_slot = md.off + md.n - 1;
+        tb.rootbox[2 * m] = f4(ul);
+        tb.rootbox[2 * m + 1] = f4(uh);
+        write_root(tb.nodes, root_slot, f4(ul), f4(uh), md.off, md.n <= L ? md.n : 0);
     }
-    __stcg(tb.lbox + 2 * (int64_t)g, lo);
-    __stcg(tb.lbox + 2 * (int64_t)g + 1, hi);
-    const int m = (int)(keys[g] >> 32);
-    if (n == 1) {
-        write_root(tb.nodes, root_slot, lo, hi, g, 1);
-        tb.rootbox[2 * m] = lo;
-        tb.rootbox[2 * m + 1] = hi;
+}
+
+// Shared-memory sparse table of one block's leaf boxes: level k holds the
+// union of the 2^k boxes starting at each position (kBoxBlock - 2^k + 1
+// entries), levels packed one after another, six float planes (lo xyz,
+// hi xyz).  The union over any range [a, b] of the block is that of two
+// overlapping entries of level floor(log2(b - a + 1)).
+constexpr int kBoxLevels = 10;  // log2(kBoxBlock) + 1
+static_assert(1 << (kBoxLevels - 1) == kBoxBlock, "kBoxBlock is a power of two");
+__host__ __device__ constexpr int st_level(int k) { return k * (kBoxBlock + 1) - ((1 << k) - 1); }
+constexpr int kStEntries = st_level(kBoxLevels);
+constexpr size_t kBoxSmem = sizeof(float) * 6 * kStEntries + 2 * sizeof(int2) * kBoxBlock;
+
+// Union of the leaf boxes at block positions [a, b] (a <= b).
+__device__ __forceinline__ void st_query(const float* st, int a, int b, float l[3], float h[3]) {
+    const int k = 31 - __clz(b - a + 1);
+    const int i = st_level(k) + a, j = st_level(k) + b - (1 << k) + 1;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        l[c] = fminf(st[c * kStEntries + i], st[c * kStEntries + j]);
+        h[c] = fmaxf(st[(3 + c) * kStEntries + i], st[(3 + c) * kStEntries + j]);
+    }
+}
+
+// a5, first pass.  One block per kBoxBlock consecutive sorted leaves, one
+// thread per leaf.  Each thread writes its triangle in leaf order and its
+// leaf box; the block builds a sparse table of its leaf boxes in shared
+// memory, from which it writes the prefix and suffix unions of every leaf
+// (tb.pre / tb.suf, for the second pass) and the traversal record of every
+// slot whose leaf range lies inside the block: each child's box is the
+// union over the child's leaf range, so no slot waits for another (the
+// paper's bottom-up pass with its per-node counters, Sec. 3.1, gives the
+// same boxes: min / max are exact in any order).  Slots whose range crosses
+// a block boundary are finished by k_boxes_span; with `list` (a build, not
+// a refit) they are appended to tb.span.
+__global__ void __launch_bounds__(kBoxBlock) k_boxes_local(MeshArgs ma, TreeBufs tb,
+                                                           const uint64_t* __restrict__ keys,
+                                                           const uint32_t* __restrict__ vals,
+                                                           int list) {
+    extern __shared__ float4 smem4[];
+    float* st = (float*)smem4;
+    int2* sch = (int2*)(st + 6 * kStEntries);  // children of slots base ..
+    int2* srg = sch + kBoxBlock;               // leaf ranges of slots base ..
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int base = blockIdx.x * kBoxBlock, g = base + tid, N = tb.N;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    MeshDesc md;
+    md.off = 0;
+    md.n = 0;
+    int m = 0;
+    if (g < N) {
+        m = (int)(keys[g] >> 32);
+        md = mesh_of(ma, m);
+        sch[tid] = *(const int2*)(tb.child + 2 * (int64_t)g);
+        srg[tid] = *(const int2*)(tb.range + 2 * (int64_t)g);
+        const int j = (int)vals[g] - md.off;
+        float3 a, b, c;
+        const bool ok = tri_vertices(md, j, tb.status, a, b, c);
+        if (!ok) a = b = c = make_float3(0.f, 0.f, 0.f);  // never hits (zero edges)
+        tb.tris[3 * (int64_t)g + 0] = make_float4(a.x, a.y, a.z, i2f(j));
+        tb.tris[3 * (int64_t)g + 1] = make_float4(b.x, b.y, b.z, 0.f);
+        tb.tris[3 * (int64_t)g + 2] = make_float4(c.x, c.y, c.z, 0.f);
+        if (ok) {  // an invalid triangle keeps the empty box (lo > hi)
+            lo[0] = fminf(fminf(a.x, b.x), c.x);
+            lo[1] = fminf(fminf(a.y, b.y), c.y);
+            lo[2] = fminf(fminf(a.z, b.z), c.z);
+            hi[0] = fmaxf(fmaxf(a.x, b.x), c.x);
+            hi[1] = fmaxf(fmaxf(a.y, b.y), c.y);
+            hi[2] = fmaxf(fmaxf(a.z, b.z), c.z);
+        }
+        __stcg(tb.lbox + 2 * (int64_t)g, f4(lo));
+        __stcg(tb.lbox + 2 * (int64_t)g + 1, f4(hi));
+        if (md.n == 1) {
+            write_root(tb.nodes, md.off, f4(lo), f4(hi), g, 1);
+            tb.rootbox[2 * m] = f4(lo);
+            tb.rootbox[2 * m + 1] = f4(hi);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        st[c * kStEntries + tid] = lo[c];
+        st[(3 + c) * kStEntries + tid] = hi[c];
+    }
+    // slots whose range crosses a block boundary, for the second pass
+    const bool inner = g < N && g - md.off < md.n - 1;  // an internal slot, not a root slot
+    const bool local = inner && srg[tid].x >= base && srg[tid].y < base + kBoxBlock;
+    if (list) {
+        const bool span = inner && !local;
+        const unsigned bal = __ballot_sync(0xffffffffu, span);
+        if (bal) {
+            int p0 = 0;
+            if (lane == 0) p0 = atomicAdd(tb.nspan, __popc(bal));
+            p0 = __shfl_sync(0xffffffffu, p0, 0);
+            if (span) {
+                const int2 rg = srg[tid], cc = sch[tid];
+                tb.span[p0 + __popc(bal & ((1u << lane) - 1u))] =
+                    make_int4(g, rg.x, rg.y, cc.x >= 0 ? cc.x : -cc.x - 1);
+            }
+        }
+    }
+    for (int k = 1; k < kBoxLevels; ++k) {
+        __syncthreads();
+        const int h = 1 << (k - 1);
+        if (tid <= kBoxBlock - 2 * h) {
+            const int s = st_level(k - 1) + tid, d = st_level(k) + tid;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                st[c * kStEntries + d] = fminf(st[c * kStEntries + s], st[c * kStEntries + s + h]);
+                st[(3 + c) * kStEntries + d] =
+                    fmaxf(st[(3 + c) * kStEntries + s], st[(3 + c) * kStEntries + s + h]);
+            }
+        }
+    }
+    __syncthreads();
+    if (g >= N) return;
+    float l0[3], h0[3];
+    st_query(st, 0, tid, l0, h0);
+    __stcg(tb.pre + 2 * (int64_t)g, f4(l0));
+    __stcg(tb.pre + 2 * (int64_t)g + 1, f4(h0));
+    st_query(st, tid, kBoxBlock - 1, l0, h0);
+    __stcg(tb.suf + 2 * (int64_t)g, f4(l0));
+    __stcg(tb.suf + 2 * (int64_t)g + 1, f4(h0));
+    if (!local) return;
+    // the record of slot g: children [first, gam] and [gam + 1, last]
+    const int2 rg = srg[tid], cc = sch[tid];
+    const int gam = cc.x >= 0 ? cc.x : -cc.x - 1;
+    if (gam < rg.x || gam >= rg.y) {
+        latch(tb.status, RSI_ERR_INTERNAL);
         return;
     }
-    int node = tb.parent[N + g];
-    // The climbing thread carries its own subtree (child code, box, first
-    // leaf, size), so after the atomic only the sibling's box and range are
-    // loaded; the node's child pair and parent (written by k_karras) are
-    // loaded before the atomic so that their latency overlaps it.
-    int me = -g - 1;
-    float4 mlo = lo, mhi = hi;
-    int mfirst = g, msize = 1;
-    // a radix tree over 62-bit keys is at most 63 levels deep
-    for (int climb = 0;; ++climb) {
-        if (climb > 70 || node < off || node >= off + n - 1) {
+    float l1[3], h1[3];
+    st_query(st, rg.x - base, gam - base, l0, h0);
+    st_query(st, gam + 1 - base, rg.y - base, l1, h1);
+    finish_node(tb, md, m, g, cc, l0, h0, rg.x, gam - rg.x + 1, l1, h1, gam + 1, rg.y - gam);
+}
+
+// Union of the leaf boxes at sorted positions [a, b], a and b in different
+// blocks of the first pass: the suffix of a's block from a, every whole block
+// in between (the suffix of its first leaf), the prefix of b's block up to b.
+// All 32 lanes call it (want == false: no range).  The lanes' whole blocks
+// are laid end to end and loaded 32 per round, one per lane; a segmented
+// scan over the lanes then merges each round's boxes into their owner's.
+__device__ __forceinline__ void span_box(const TreeBufs& tb, bool want, int a, int b, float l[3],
+                                         float h[3]) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    l[0] = l[1] = l[2] = INFINITY;
+    h[0] = h[1] = h[2] = -INFINITY;
+    int q0 = 0, cnt = 0;  // whole blocks [q0, q0 + cnt)
+    if (want) {
+        merge_box(l, h, __ldcg(tb.suf + 2 * (int64_t)a), __ldcg(tb.suf + 2 * (int64_t)a + 1));
+        merge_box(l, h, __ldcg(tb.pre + 2 * (int64_t)b), __ldcg(tb.pre + 2 * (int64_t)b + 1));
+        q0 = a / kBoxBlock + 1;
+        cnt = b / kBoxBlock - q0;
+        if (cnt < 0) cnt = 0;
+    }
+    int inc = cnt;  // items [inc - cnt, inc) of the laid-out list are this lane's
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const int total = __shfl_sync(FULL, inc, 31);
+    const int exc = inc - cnt;
+    for (int r0 = 0; r0 < total; r0 += 32) {
+        const int j = r0 + lane;
+        int own = 0;  // the lane whose items hold j: lanes with inc <= j come before it
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (__shfl_sync(FULL, inc, own + step - 1) <= j) own += step;
+        const int oq0 = __shfl_sync(FULL, q0, own), oexc = __shfl_sync(FULL, exc, own);
+        float wl[3] = {INFINITY, INFINITY, INFINITY}, wh[3] = {-INFINITY, -INFINITY, -INFINITY};
+        if (j < total) {
+            const int64_t p = 2 * (int64_t)(oq0 + (j - oexc)) * kBoxBlock;
+            merge_box(wl, wh, __ldcg(tb.suf + p), __ldcg(tb.suf + p + 1));
+        }
+        // inclusive scan within each owner's run of lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int oo = __shfl_up_sync(FULL, own, o);
+            float yl[3], yh[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                yl[k] = __shfl_up_sync(FULL, wl[k], o);
+                yh[k] = __shfl_up_sync(FULL, wh[k], o);
+            }
+            if (lane >= o && oo == own) merge_box(wl, wh, f4(yl), f4(yh));
+        }
+        // each owner takes the union from the last lane of its run
+        const bool mine = cnt > 0 && exc < r0 + 32 && inc > r0;
+        const int src = mine ? min(inc, r0 + 32) - 1 - r0 : lane;
+        float tl[3], th[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            tl[k] = __shfl_sync(FULL, wl[k], src);
+            th[k] = __shfl_sync(FULL, wh[k], src);
+        }
+        if (mine) merge_box(l, h, f4(tl), f4(th));
+    }
+}
+
+// Box of the child of a second-pass slot that covers leaves [a, b] (code c:
+// Karras child code): a leaf box, the box of a slot the first pass finished,
+// or the union over the blocks its range crosses.  All 32 lanes call it.
+__device__ __forceinline__ void child_box(const TreeBufs& tb, bool act, int c, int a, int b,
+                                          float l[3], float h[3]) {
+    const bool wide = act && a / kBoxBlock != b / kBoxBlock;
+    if (act && !wide) {
+        const float4* p = c < 0 ? tb.lbox + 2 * (int64_t)a : tb.nbox + 2 * (int64_t)c;
+        const float4 lo = __ldcg(p), hi = __ldcg(p + 1);
+        l[0] = lo.x; l[1] = lo.y; l[2] = lo.z;
+        h[0] = hi.x; h[1] = hi.y; h[2] = hi.z;
+    }
+    float wl[3], wh[3];
+    span_box(tb, wide, a, b, wl, wh);
+    if (wide) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            l[k] = wl[k];
+            h[k] = wh[k];
+        }
+    }
+}
+
+// a5, second pass: the slots listed by the first pass (leaf range across a
+// block boundary), each independently.  A list entry holds the slot, its
+// leaf range [first, last] and its split g (the last leaf of the left
+// child): the left child is leaf g when first == g, else slot g; the right
+// child leaf g + 1 when last == g + 1, else slot g + 1 (Karras numbering).
+// The children's boxes come from the first pass (leaf boxes, finished
+// slots) or from the prefix / suffix unions (children that cross a boundary
+// themselves); no slot waits for another.
+__global__ void __launch_bounds__(128) k_boxes_span(MeshArgs ma, TreeBufs tb,
+                                                    const uint64_t* __restrict__ keys) {
+    const int cnt = *tb.nspan;
+    const int lane = threadIdx.x & 31;
+    const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int k0 = wg * 32; k0 < cnt; k0 += nw * 32) {  // warp-uniform
+        const int k = k0 + lane;
+        const bool act = k < cnt;
+        int4 e = make_int4(0, 0, 0, 0);
+        if (act) e = __ldcg(tb.span + k);
+        const int node = e.x, first = e.y, last = e.z, gam = e.w;
+        const bool ok = act && first >= 0 && gam >= first && gam < last && last < tb.N;
+        if (act && !ok) latch(tb.status, RSI_ERR_INTERNAL);
+        const int2 cc = make_int2(first == gam ? -gam - 1 : gam,
+                                  last == gam + 1 ? -gam - 2 : gam + 1);
+        float l0[3], h0[3], l1[3], h1[3];
+        child_box(tb, ok, cc.x, first, gam, l0, h0);
+        child_box(tb, ok, cc.y, gam + 1, last, l1, h1);
+        if (!ok) continue;
+        const int m = (int)(keys[first] >> 32);
+        const MeshDesc md = mesh_of(ma, m);
+        if (node < md.off || node >= md.off + md.n - 1) {
             latch(tb.status, RSI_ERR_INTERNAL);
-            return;
+            continue;
         }
-        const int2 cc = *(const int2*)(tb.child + 2 * (int64_t)node);
-        const int par = tb.parent[node];
-        // acquire-release: the first arrival publishes its child's box and
-        // node record, the second arrival sees them
-        if (atomic_add_acq_rel(&tb.flag[node], 1) == 0) return;  // the sibling finishes it
-        const bool mine0 = cc.x == me;
-        const int x = mine0 ? cc.y : cc.x;  // the sibling
-        float4 slo, shi;
-        int sfirst, ssize;
-        if (x < 0) {
-            const int leaf = -x - 1;
-            slo = __ldcg(tb.lbox + 2 * (int64_t)leaf);
-            shi = __ldcg(tb.lbox + 2 * (int64_t)leaf + 1);
-            sfirst = leaf;
-            ssize = 1;
-        } else {
-            slo = __ldcg(tb.nbox + 2 * (int64_t)x);
-            shi = __ldcg(tb.nbox + 2 * (int64_t)x + 1);
-            const int2 rg = *(const int2*)(tb.range + 2 * (int64_t)x);
-            sfirst = rg.x;
-            ssize = rg.y - rg.x + 1;
-        }
-        // children in the node's order: 0 = cc.x, 1 = cc.y
-        const float4 l0 = mine0 ? mlo : slo, h0 = mine0 ? mhi : shi;
-        const float4 l1 = mine0 ? slo : mlo, h1 = mine0 ? shi : mhi;
-        const int f0 = mine0 ? mfirst : sfirst, z0 = mine0 ? msize : ssize;
-        const int f1 = mine0 ? sfirst : mfirst, z1 = mine0 ? ssize : msize;
-        const int ref0 = z0 <= L ? f0 : cc.x, cnt0 = z0 <= L ? z0 : 0;
-        const int ref1 = z1 <= L ? f1 : cc.y, cnt1 = z1 <= L ? z1 : 0;
-        const float4 ulo = make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.f);
-        const float4 uhi = make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.f);
-        __stcg(tb.nbox + 2 * (int64_t)node, ulo);
-        __stcg(tb.nbox + 2 * (int64_t)node + 1, uhi);
-        write_node(tb.nodes, node, l0, h0, ref0, cnt0, l1, h1, ref1, cnt1);
-        if (node == off) {  // Karras root: fill the root slot
-            tb.rootbox[2 * m] = ulo;
-            tb.rootbox[2 * m + 1] = uhi;
-            if (n <= L)
-                write_root(tb.nodes, root_slot, ulo, uhi, off, n);
-            else
-                write_root(tb.nodes, root_slot, ulo, uhi, off, 0);
-            return;
-        }
-        me = node;
-        mlo = ulo;
-        mhi = uhi;
-        mfirst = f0 < f1 ? f0 : f1;
-        msize = z0 + z1;
-        node = par;
+        finish_node(tb, md, m, node, cc, l0, h0, first, gam - first + 1, l1, h1, gam + 1,
+                    last - gam);
     }
 }
 
@@ -520,6 +698,23 @@ __global__ void __launch_bounds__(1024) k_treelet(TreeBufs tb, int root_slot, in
 // ---------------------------------------------------------------- host
 static inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// The first box pass takes more than the default 48 KB of dynamic shared
+// memory; its limit is raised once per device.
+static std::mutex g_box_mu;
+static uint64_t g_box_dev = 0;  // bit d: raised on device d
+
+static cudaError_t box_smem_limit() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_box_mu);
+    if (dev < 64 && ((g_box_dev >> dev) & 1ull)) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_boxes_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kBoxSmem);
+    if (e == cudaSuccess && dev < 64) g_box_dev |= 1ull << dev;
+    return e;
+}
+
 cudaError_t build_tree(TreeBufs& tb, const MeshArgs& ma, cudaStream_t s, bool refit) {
     const int N = tb.N;
     if (N == 0) return cudaSuccess;
@@ -536,11 +731,12 @@ cudaError_t build_tree(TreeBufs& tb, const MeshArgs& ma, cudaStream_t s, bool re
         if (e != cudaSuccess) return e;
         tb.sorted = cur;
         k_karras<<<cdiv(N, 256), 256, 0, s>>>(ma, tb, tb.keys[cur]);
-    } else {
-        cudaError_t e = cudaMemsetAsync(tb.flag, 0, sizeof(int32_t) * (size_t)N, s);
-        if (e != cudaSuccess) return e;
     }
-    k_climb<<<cdiv(N, 256), 256, 0, s>>>(ma, tb, tb.keys[tb.sorted], tb.vals[tb.sorted]);
+    cudaError_t e = box_smem_limit();
+    if (e != cudaSuccess) return e;
+    k_boxes_local<<<cdiv(N, kBoxBlock), kBoxBlock, kBoxSmem, s>>>(ma, tb, tb.keys[tb.sorted],
+                                                         tb.vals[tb.sorted], refit ? 0 : 1);
+    k_boxes_span<<<cdiv(N, 4096), 128, 0, s>>>(ma, tb, tb.keys[tb.sorted]);
     if (tb.M == 1 && tb.top_levels > 0) k_treelet<<<1, 1024, 0, s>>>(tb, N - 1, tb.top_levels);
     return cudaGetLastError();
 }

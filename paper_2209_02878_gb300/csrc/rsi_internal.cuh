@@ -7,8 +7,12 @@
 //   child[2N]        Karras children of internal slot g: >= 0 internal slot,
 //                    < 0 leaf -(global sorted position + 1)
 //   range[2N]        first, last leaf (global sorted positions) of slot g
-//   parent[2N]       [0,N): parent of internal slot, [N,2N): parent of leaf
 //   nbox/lbox[2N]    float4 lo, hi boxes of internal slots / leaves
+//   pre/suf[2N]      float4 lo, hi unions of the leaf boxes of each block of
+//                    kBoxBlock sorted leaves up to / from each leaf
+//   span[N]          internal slots whose leaf range crosses such a block
+//                    boundary, {slot, first, last, split} (their boxes come
+//                    from pre / suf)
 //   nodes[4N]        traversal node per slot = 4 x float4 = 64 B, the two
 //                    children's coordinates interleaved in pairs so that one
 //                    packed f32x2 operation serves both child boxes:
@@ -47,6 +51,7 @@ constexpr int kSortTileMin = kSortThreads * 4;         // 1024 keys per tile (sm
 constexpr int kSortBins = 256;
 constexpr int kBuildThreads = 256;
 constexpr int kBuildChunk = 512;    // triangles per block in bounds / Morton
+constexpr int kBoxBlock = 512;      // sorted leaves per block of the bottom-up box pass
 
 // FP32 filter constants (see mt32 below).
 constexpr float kFilterK = 0x1p-17f;
@@ -91,8 +96,11 @@ struct TreeBufs {
     float4* rootbox;  // 2 * M: box of each mesh (lo, hi)
     int32_t* child;   // 2N
     int32_t* range;   // 2N
-    int32_t* parent;  // 2N
-    int32_t* flag;    // N
+    int4* span;       // N: slots whose leaf range crosses a box-pass block
+                      // {slot, first leaf, last leaf, split}
+    int32_t* nspan;   // entries of span
+    float4* pre;      // 2N: union of the leaf boxes from the box-pass block's first leaf
+    float4* suf;      // 2N: union of the leaf boxes to the box-pass block's last leaf
     float4* nbox;     // 2N
     float4* lbox;     // 2N
     float4* nodes;    // 4N
