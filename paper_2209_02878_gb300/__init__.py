@@ -124,11 +124,23 @@ def _mode(mode) -> int:
         raise ValueError(f"unknown mode {mode!r}; use one of {sorted(MODES)}") from None
 
 
-def _launch(launch):
+def _launch(launch, n=None, device=None):
+    """rsi_launch_opts from a dict; "order" is an int32 CUDA tensor of n
+    entries (a processing order, e.g. from BVH.segment_order)."""
     lo = _abi.rsi_launch_opts()
     if launch:
         for k, v in launch.items():
-            setattr(lo, k, int(v))
+            if k == "order":
+                if v is None:
+                    continue
+                _check_tensor(v, "order", torch.int32, cols=0)
+                if v.dim() != 1 or (n is not None and v.shape[0] != n):
+                    raise ValueError("order must be a 1-D int32 tensor with one entry per segment")
+                if device is not None and v.device != device:
+                    raise ValueError("order must be on the segments' device")
+                lo.order = v.data_ptr()
+            else:
+                setattr(lo, k, int(v))
     return lo
 
 
@@ -258,7 +270,7 @@ class BVH:
         n = int(A.shape[0])
         o = out if out is not None else _alloc_outputs(m, n, A.device, compact, hit_cap)
         ro = _rsi_output(o)
-        lo = _launch(launch)
+        lo = _launch(launch, n, A.device)
         with torch.cuda.device(self.device):
             if stats:
                 st = _abi.rsi_stats()
@@ -272,6 +284,23 @@ class BVH:
                                                    C.byref(lo), _stream(stream)),
                            "rsi_intersect")
         return o
+
+    def segment_order(self, A, B, bits=0, stream=None):
+        """Coherent processing order of the segments A[i] -> B[i] (float32
+        [nR,3], CUDA) with rsi_segment_order: an int32 permutation to pass as
+        launch={"order": ...} to later intersect calls on the same segments
+        (bits 6..30, 0 -> 30)."""
+        _check_tensor(A, "A", torch.float32)
+        _check_tensor(B, "B", torch.float32)
+        if A.shape != B.shape:
+            raise ValueError("A and B must have the same shape")
+        n = int(A.shape[0])
+        order = torch.empty(n, dtype=torch.int32, device=A.device)
+        with torch.cuda.device(self.device):
+            _abi.check(self._lib.rsi_segment_order(self._h, _vp(A), _vp(B), n, int(bits),
+                                                   _vp(order), _stream(stream)),
+                       "rsi_segment_order")
+        return order
 
     def intersect_host(self, A, B, mode="bool", *, out=None, chunk=0, launch=None,
                        stream=None):
@@ -397,15 +426,18 @@ class RSIFunction(torch.autograd.Function):
     fixed in the backward pass (rsi_intersect_backward).  With a `bvh` passed
     the tree is reused across calls and kept current: refit when V is
     another tensor or was changed in place (an optimizer step) since the
-    tree last saw it, rebuilt when T is another tensor (BVH.sync)."""
+    tree last saw it, rebuilt when T is another tensor (BVH.sync).  `order`:
+    a processing order of the segments (BVH.segment_order), reused while A
+    and B stay the same."""
 
     @staticmethod
-    def forward(ctx, V, A, B, T, bvh):
+    def forward(ctx, V, A, B, T, bvh, order=None):
         if bvh is None:
             bvh = BVH(V.detach(), T)
         else:
             bvh.sync(V.detach(), T)
-        o = bvh.intersect(A.detach(), B.detach(), "nearest")
+        o = bvh.intersect(A.detach(), B.detach(), "nearest",
+                          launch={"order": order} if order is not None else None)
         ctx.save_for_backward(V.detach(), A.detach(), B.detach(), T, o["tri"])
         ctx.mark_non_differentiable(o["tri"])
         return o["point"], o["tuv"], o["tri"]
@@ -416,13 +448,15 @@ class RSIFunction(torch.autograd.Function):
         gV, gA, gB = intersect_backward(V, T, A, B, tri, g_point, g_tuv)
         return (gV if ctx.needs_input_grad[0] else None,
                 gA if ctx.needs_input_grad[1] else None,
-                gB if ctx.needs_input_grad[2] else None, None, None)
+                gB if ctx.needs_input_grad[2] else None, None, None, None)
 
 
-def nearest_hit(V, T, A, B, bvh=None):
+def nearest_hit(V, T, A, B, bvh=None, order=None):
     """Differentiable nearest crossing: (point, tuv, tri).  Pass a BVH of
-    (V, T) to reuse it across steps: it is refit whenever V has moved."""
-    return RSIFunction.apply(V, A, B, T, bvh)
+    (V, T) to reuse it across steps: it is refit whenever V has moved.  Pass
+    order=bvh.segment_order(A, B) to traverse fixed segments in a coherent
+    order computed once."""
+    return RSIFunction.apply(V, A, B, T, bvh, order)
 
 
 class Batch:

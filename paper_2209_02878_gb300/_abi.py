@@ -47,7 +47,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p)
 
 class rsi_launch_opts(C.Structure):
     _fields_ = [("block_size", i32), ("stack_depth", i32), ("smem_nodes", i32), ("stats", i32),
-                ("sort_bits", i32), ("node_width", i32), ("packet", i32)]
+                ("sort_bits", i32), ("node_width", i32), ("packet", i32), ("order", vp)]
 
 
 class rsi_output(C.Structure):
@@ -91,6 +91,7 @@ _PROTOS = {
     "rsi_bvh_destroy": (C.c_int, [vp]),
     "rsi_bvh_export": (C.c_int, [vp, vp] + [vp] * 9),
     "rsi_intersect": (C.c_int, [vp, vp, vp, i64, C.c_int, P(rsi_output), P(rsi_launch_opts), vp]),
+    "rsi_segment_order": (C.c_int, [vp, vp, vp, i64, i32, vp, vp]),
     "rsi_intersect_host": (C.c_int, [vp, vp, vp, i64, C.c_int, P(rsi_output), i64,
                                      P(rsi_launch_opts), vp]),
     "rsi_points_inside": (C.c_int, [vp, vp, i64, vp, P(rsi_launch_opts), vp]),

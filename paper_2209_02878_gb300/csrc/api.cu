@@ -89,6 +89,7 @@ rsi_status check_build_opts(const rsi_build_opts* o, int32_t* leaf, int32_t* lev
 struct LaunchCfg {
     int block, stack, smem_nodes, sort_bits, width;
     bool stats, packet;
+    const int32_t* order;
 };
 
 rsi_status check_launch_opts(const rsi_launch_opts* lo, bool has_treelet, LaunchCfg* c) {
@@ -99,8 +100,10 @@ rsi_status check_launch_opts(const rsi_launch_opts* lo, bool has_treelet, Launch
     c->width = 2;
     c->stats = false;
     c->packet = false;
+    c->order = nullptr;
     int sm = 0;
     if (lo) {
+        c->order = lo->order;
         if (lo->block_size != 0) {
             if (lo->block_size < 32 || lo->block_size > 1024 || lo->block_size % 32) return RSI_ERR_ARG;
             c->block = lo->block_size;
@@ -501,11 +504,11 @@ static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, in
     P.max_visits = (int)h->nT + 2;
     P.status = h->tb.status;
     P.out = trav_out(mode, out);
-    P.order = nullptr;
+    P.order = c.order;  // the caller's order, else sort_bits
     P.ready = ready;
     P.ready_chunk = ready_chunk;
     const int bits = c.sort_bits;  // 0 or -1: input order
-    if (bits > 0 && h->nT > 0 && nR < ((int64_t)1 << 31)) {
+    if (!c.order && bits > 0 && h->nT > 0 && nR < ((int64_t)1 << 31)) {
         st = ensure_seg_ws(h, nR, (cudaStream_t)s);
         if (st != RSI_OK) return st;
         RSI_CK(rsi::segment_order(dA, dB, (int)nR, h->tb.rootbox, bits, h->seg_ws,
@@ -522,6 +525,33 @@ static rsi_status intersect_impl(rsi_bvh h, const float* dA, const float* dB, in
     else
         RSI_CK(rsi::launch_trace(P, mode, c.stack, c.stats, c.block, c.width, (cudaStream_t)s));
     return RSI_OK;
+}
+
+static rsi_status segment_order_impl(rsi_bvh h, const float* dA, const float* dB, int64_t nR,
+                                     int32_t bits, int32_t* dOrder, rsi_stream s) {
+    if (!h || nR < 0 || nR >= ((int64_t)1 << 31)) return RSI_ERR_ARG;
+    if (bits == 0) bits = 30;
+    if (bits < 6 || bits > 30) return RSI_ERR_ARG;
+    if (!h->built) return RSI_ERR_NOT_BUILT;
+    if (nR == 0) return RSI_OK;
+    if (!dA || !dB || !dOrder) return RSI_ERR_ARG;
+    rsi_status st = ensure_seg_ws(h, nR, (cudaStream_t)s);
+    if (st != RSI_OK) return st;
+    // an empty mesh has no box: the keys are then arbitrary, and the sorted
+    // values still a permutation
+    const int32_t* ord = nullptr;
+    RSI_CK(rsi::segment_order(dA, dB, (int)nR, h->tb.rootbox, bits, h->seg_ws, (cudaStream_t)s,
+                              &ord));
+    RSI_CK(cudaMemcpyAsync(dOrder, ord, 4 * (size_t)nR, cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)s));
+    return RSI_OK;
+}
+
+rsi_status rsi_segment_order(rsi_bvh h, const float* dA, const float* dB, int64_t nR,
+                             int32_t bits, int32_t* dOrder, rsi_stream s) {
+    const rsi_status st = segment_order_impl(h, dA, dB, nR, bits, dOrder, s);
+    if (h) h->stream = (cudaStream_t)s;
+    return st;
 }
 
 rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR, rsi_mode mode,
@@ -682,6 +712,7 @@ static rsi_status intersect_host_impl(rsi_bvh h, const float* hA, const float* h
     rsi_status st = check_output(mode, hout);
     if (st != RSI_OK) return st;
     if (hout->hit_idx) return RSI_ERR_ARG;  // no compaction from host buffers
+    if (lo && lo->order) return RSI_ERR_ARG;  // an order indexes device-resident segments
     rsi_launch_opts lo2;
     memset(&lo2, 0, sizeof(lo2));
     if (lo) lo2 = *lo;
@@ -806,7 +837,7 @@ rsi_status rsi_intersect_host(rsi_bvh h, const float* hA, const float* hB, int64
 
 static rsi_status points_inside_impl(rsi_bvh h, const float* dP, int64_t nP, uint8_t* dInside,
                                      const rsi_launch_opts* lo, rsi_stream s) {
-    if (!h || nP < 0) return RSI_ERR_ARG;
+    if (!h || nP < 0 || (lo && lo->order)) return RSI_ERR_ARG;
     if (!h->built) return RSI_ERR_NOT_BUILT;
     if (nP == 0) return RSI_OK;
     if (!dP || !dInside) return RSI_ERR_ARG;
@@ -896,6 +927,7 @@ rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_bu
     LaunchCfg cfg;
     st = check_launch_opts(lo, false, &cfg);
     if (st != RSI_OK) return st;
+    if (cfg.order) return RSI_ERR_ARG;  // one order cannot serve several items
     int64_t N = 0;
     int nblk = 0;
     std::vector<MeshDesc> table(n);

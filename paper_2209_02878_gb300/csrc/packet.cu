@@ -66,8 +66,16 @@ __global__ void __maxnreg__(PacketRegs<MODE>::value) k_trace_packet(TraceParams 
         b = __shfl_sync(FULL, b, 0);
         if (b >= (unsigned long long)P.nR) break;
         const int64_t pos = (int64_t)b + lane;
-        const bool valid = pos < P.nR;
-        const int64_t i = valid ? (C.order ? (int64_t)C.order[pos] : pos) : 0;
+        bool valid = pos < P.nR;
+        int64_t i = pos;
+        if (valid && C.order) {  // a caller's order: entries outside [0, nR) are skipped
+            i = C.order[pos];
+            if (i < 0 || i >= P.nR) {
+                atomicCAS(C.status, 0, RSI_ERR_BAD_INDEX);
+                valid = false;
+            }
+        }
+        if (!valid) i = 0;
         Seg s;
         Result res;
         result_init(res);

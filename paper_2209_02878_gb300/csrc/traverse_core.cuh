@@ -630,16 +630,21 @@ __device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long
             const int avail = left < (int64_t)__popc(idle) ? (int)left : __popc(idle);
             if (i < 0 && (int)__popc(idle & lt) < avail) {
                 int64_t k = pool + __popc(idle & lt);
-                if (C.order) k = C.order[k];
+                bool known = true;
+                if (C.order) {  // a caller's order: entries outside [0, nR) are skipped
+                    k = C.order[k];
+                    known = k >= 0 && k < C.nR;
+                    if (!known) atomicCAS(C.status, 0, RSI_ERR_BAD_INDEX);
+                }
                 if (STATS) ++segs;
                 result_init(res);
-                if (seg_setup(C.A, C.B, k, s) && C.root != kNoRoot) {
+                if (known && seg_setup(C.A, C.B, k, s) && C.root != kNoRoot) {
                     i = k;
                     node = W == 4 ? C.root4 : C.root;
                     sp = 0;
                     visits = 0;
                     tlim = 1.f;
-                } else {  // non-finite segment or empty mesh: a miss
+                } else if (known) {  // non-finite segment or empty mesh: a miss
                     float dist, P[3];
                     write_result<MODE, STATS>(C.out, s, false, C.A, C.B, k, C.tris, res, dist, P,
                                               st);
