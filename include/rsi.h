@@ -329,8 +329,8 @@ rsi_status rsi_intersect(rsi_bvh h, const float* dA, const float* dB, int64_t nR
  * (DEVICE int32[nR], a permutation of [0, nR)) on s.  Uses the handle's
  * segment-order workspace (16 B per segment, allocated on first use from the
  * device allocator, on s).  Measured on 262,144 near-vertical segments over
- * a 131,072-triangle heightfield: nearest traversal 22 % faster than in input
- * order; random segments gain nothing.  Errors: RSI_ERR_ARG (NULL pointer,
+ * a 131,072-triangle heightfield: nearest traversal 0.227 -> 0.185 ms against
+ * input order; random segments gain nothing.  Errors: RSI_ERR_ARG (NULL pointer,
  * nR < 0 or >= 2^31, bits out of range), RSI_ERR_NOT_BUILT, RSI_ERR_OOM,
  * RSI_ERR_CUDA. */
 rsi_status rsi_segment_order(rsi_bvh h, const float* dA, const float* dB, int64_t nR,
