@@ -715,6 +715,17 @@ def run_case(args):
             gV = torch.zeros_like(V)
             fn = lambda: rsi.intersect_backward(V, T, A, B, tri, grad_point=W, grad_V=gV,  # noqa: E731
                                                 stream=stream)
+        elif args.case == "build":
+            # the LBVH build and a refit of the 29,768- and 131,072-triangle
+            # heightfields, alternately (the box pass writes the same trees)
+            meshes = [synth.workload_paper_bool(n_seg=1)[0], synth.workload_diff(n_seg=1)[0]]
+            tens = [(t(m.V), t(m.T)) for m in meshes]
+            bvhs = [rsi.BVH(V, T, stream=stream) for V, T in tens]
+
+            def fn():
+                for b, (V, T) in zip(bvhs, tens):
+                    b.build(V, T, stream=stream)
+                    b.refit(V, stream=stream)
         else:  # batched
             items = synth.workload_batched()
             tens = [(t(m.V), t(m.T), t(sg.A), t(sg.B), mode) for m, sg, mode in items]
@@ -737,7 +748,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly")
     ap.add_argument("--case", choices=["sphere_nearest", "coherent_packet", "diff_nearest",
-                                       "diff_backward", "batched"],
+                                       "diff_backward", "batched", "build"],
                     help="run one secondary kernel --steps times for a profiler capture")
     args = ap.parse_args()
     if args.case:
