@@ -258,6 +258,7 @@ rsi_status rsi_bvh_create(int64_t nV, int64_t nT, const rsi_build_opts* opt, rsi
     if (st != RSI_OK) return st;
     int device = 0;
     RSI_CK(cudaGetDevice(&device));
+    RSI_CK(rsi::build_prepare());
     rsi_bvh h = new rsi_bvh_s();
     h->hooks = rsi::current_hooks();
     h->device = device;
@@ -928,6 +929,7 @@ rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_bu
     st = check_launch_opts(lo, false, &cfg);
     if (st != RSI_OK) return st;
     if (cfg.order) return RSI_ERR_ARG;  // one order cannot serve several items
+    RSI_CK(rsi::build_prepare());
     int64_t N = 0;
     int nblk = 0;
     std::vector<MeshDesc> table(n);

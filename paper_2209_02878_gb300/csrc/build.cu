@@ -703,7 +703,7 @@ static inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 static std::mutex g_box_mu;
 static uint64_t g_box_dev = 0;  // bit d: raised on device d
 
-static cudaError_t box_smem_limit() {
+cudaError_t build_prepare() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -732,7 +732,7 @@ cudaError_t build_tree(TreeBufs& tb, const MeshArgs& ma, cudaStream_t s, bool re
         tb.sorted = cur;
         k_karras<<<cdiv(N, 256), 256, 0, s>>>(ma, tb, tb.keys[cur]);
     }
-    cudaError_t e = box_smem_limit();
+    cudaError_t e = build_prepare();
     if (e != cudaSuccess) return e;
     k_boxes_local<<<cdiv(N, kBoxBlock), kBoxBlock, kBoxSmem, s>>>(ma, tb, tb.keys[tb.sorted],
                                                          tb.vals[tb.sorted], refit ? 0 : 1);

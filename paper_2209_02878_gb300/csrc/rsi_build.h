@@ -11,6 +11,11 @@ namespace rsi {
 // treelet) of the meshes described by `ma` into the buffers of `tb` on s.
 cudaError_t build_tree(TreeBufs& tb, const MeshArgs& ma, cudaStream_t s, bool refit);
 
+// Raise the box pass's shared-memory limit on the current device (once per
+// device; handle creation calls it, so that a first build captured into a
+// graph makes no attribute call).
+cudaError_t build_prepare();
+
 // Enqueue the 4-wide records of every slot (needs a completed build).
 cudaError_t build_nodes4(const TreeBufs& tb, cudaStream_t s);
 
