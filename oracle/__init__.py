@@ -63,6 +63,10 @@ def _bind(lib):
     lib.orc_mt.argtypes = [P] * 6
     lib.orc_morton3.argtypes = [C.c_uint32] * 3
     lib.orc_morton3.restype = C.c_uint32
+    lib.orc_morton2.argtypes = [C.c_uint32] * 2
+    lib.orc_morton2.restype = C.c_uint32
+    lib.orc_lbvh_h.argtypes = [P, L, P, L, C.c_int] + [P] * 8
+    lib.orc_lbvh_h.restype = C.c_int
     lib.orc_num_threads.restype = C.c_int
     return lib
 
@@ -104,6 +108,12 @@ def mt(a, b, v0, v1, v2):
 def morton3(x: int, y: int, z: int) -> int:
     """30-bit Morton interleave (Sec. 2: bit-wise interleaving of q_j)."""
     return int(_get().orc_morton3(x, y, z))
+
+
+def morton2(x: int, y: int) -> int:
+    """30-bit interleave of two 15-bit coordinates, the first one high: the
+    height-field variant of the code (a library option, not the paper's)."""
+    return int(_get().orc_morton2(x, y))
 
 
 def _alloc_outputs(nR):
@@ -200,9 +210,11 @@ def eval_fixed(V64, T, A64, B64, tri):
     return out
 
 
-def lbvh(V, T) -> dict:
+def lbvh(V, T, height_axis: int = 0) -> dict:
     """LBVH build by its plain definition (Sec. 2: centroids, support interval,
-    quantisation, Morton codes, sort, radix tree, boxes)."""
+    quantisation, Morton codes, sort, radix tree, boxes).  height_axis 1, 2
+    or 3: the library's height-field option (that coordinate left out of the
+    code, the other two quantised to 15 bits each); 0: the paper's code."""
     V, T = _f32(V), _i32(T)
     n = T.shape[0]
     o = dict(bounds=np.zeros(6, np.float32), codes=np.zeros(n, np.uint32),
@@ -211,9 +223,11 @@ def lbvh(V, T) -> dict:
              range=np.zeros((max(n - 1, 0), 2), np.int32),
              nbox=np.zeros((max(n - 1, 0), 6), np.float32),
              lbox=np.zeros((n, 6), np.float32))
-    rc = _get().orc_lbvh(_p(V), V.shape[0], _p(T), n, _p(o["bounds"]), _p(o["codes"]),
-                         _p(o["order"]), _p(o["left"]), _p(o["right"]), _p(o["range"]),
-                         _p(o["nbox"]), _p(o["lbox"]))
+    rc = _get().orc_lbvh_h(_p(V), V.shape[0], _p(T), n, int(height_axis), _p(o["bounds"]),
+                           _p(o["codes"]), _p(o["order"]), _p(o["left"]), _p(o["right"]),
+                           _p(o["range"]), _p(o["nbox"]), _p(o["lbox"]))
+    if rc == 2:
+        raise ValueError("oracle: height_axis must be 0, 1, 2 or 3")
     if rc:
         raise ValueError("oracle: triangle index out of range")
     return o

@@ -556,6 +556,21 @@ static uint32_t interleave10(uint32_t x, uint32_t y, uint32_t z) {
 
 uint32_t orc_morton3(uint32_t x, uint32_t y, uint32_t z) { return interleave10(x, y, z); }
 
+/* Height-field variant (not in the paper, an option of the library): the
+ * centroid coordinate along the height axis is left out and the two others
+ * are quantised to 15 bits each, interleaved first-axis-high:
+ * bit 2k+1 = bit k of the first kept axis, bit 2k = bit k of the second. */
+static uint32_t interleave15x2(uint32_t x, uint32_t y) {
+    uint32_t c = 0;
+    for (int k = 0; k < 15; ++k) {
+        c |= ((x >> k) & 1u) << (2 * k + 1);
+        c |= ((y >> k) & 1u) << (2 * k);
+    }
+    return c;
+}
+
+uint32_t orc_morton2(uint32_t x, uint32_t y) { return interleave15x2(x, y); }
+
 static uint64_t* g_keys;
 static int cmp_key(const void* x, const void* y) {
     uint64_t a = g_keys[*(const uint32_t*)x], b = g_keys[*(const uint32_t*)y];
@@ -581,9 +596,12 @@ static int clz64(uint64_t x) {
  *   range[2(nT-1)]  first, last leaf of each internal node
  *   nbox[6(nT-1)]   internal node boxes (lo xyz, hi xyz)
  *   lbox[6 nT]      leaf boxes by sorted position                      */
-int orc_lbvh(const float* V, long nV, const int32_t* T, long nT, float* bounds,
-             uint32_t* codes, uint32_t* order, int32_t* left, int32_t* right,
-             int32_t* range, float* nbox, float* lbox) {
+/* height_axis: 0 = the paper's code over x, y, z; 1, 2, 3 = leave out x, y
+ * or z (the height-field variant above). */
+int orc_lbvh_h(const float* V, long nV, const int32_t* T, long nT, int height_axis,
+               float* bounds, uint32_t* codes, uint32_t* order, int32_t* left, int32_t* right,
+               int32_t* range, float* nbox, float* lbox) {
+    if (height_axis < 0 || height_axis > 3) return 2;
     if (nT <= 0) return 0;
     for (long j = 0; j < 3 * nT; ++j)
         if (T[j] < 0 || T[j] >= nV) return 1;
@@ -611,22 +629,28 @@ int orc_lbvh(const float* V, long nV, const int32_t* T, long nT, float* bounds,
         bounds[3 + k] = hi[k];
     }
     uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * nT);
+    const float levels = height_axis ? 32768.0f : 1024.0f;
     for (long j = 0; j < nT; ++j) {
         uint32_t q[3];
         for (int k = 0; k < 3; ++k) {
             float ext = hi[k] - lo[k];
             if (ext > 0.0f) {
                 float s = (c[3 * j + k] - lo[k]) / ext;
-                s = s * 1024.0f;
+                s = s * levels;
                 float f = floorf(s);
                 if (f < 0.0f) f = 0.0f;
-                if (f > 1023.0f) f = 1023.0f;
+                if (f > levels - 1.0f) f = levels - 1.0f;
                 q[k] = (uint32_t)f;
             } else {
                 q[k] = 0;
             }
         }
-        codes[j] = interleave10(q[0], q[1], q[2]);
+        if (height_axis == 0) {
+            codes[j] = interleave10(q[0], q[1], q[2]);
+        } else {
+            const int a = height_axis == 1 ? 1 : 0, b = height_axis == 3 ? 1 : 2;
+            codes[j] = interleave15x2(q[a], q[b]);
+        }
         key[j] = ((uint64_t)codes[j] << 32) | (uint64_t)j;
         order[j] = (uint32_t)j;
     }
@@ -701,4 +725,10 @@ int orc_lbvh(const float* V, long nV, const int32_t* T, long nT, float* bounds,
     free(key);
     free(c);
     return 0;
+}
+
+int orc_lbvh(const float* V, long nV, const int32_t* T, long nT, float* bounds,
+             uint32_t* codes, uint32_t* order, int32_t* left, int32_t* right,
+             int32_t* range, float* nbox, float* lbox) {
+    return orc_lbvh_h(V, nV, T, nT, 0, bounds, codes, order, left, right, range, nbox, lbox);
 }

@@ -34,7 +34,8 @@ MUTANTS = {
                                 "c |= ((z >> k) & 1u) << (3 * k + 2);"),
                                ("c |= ((z >> k) & 1u) << (3 * k);",
                                 "c |= ((x >> k) & 1u) << (3 * k);")],
-    "quantisation scale 1023": [("s = s * 1024.0f;", "s = s * 1023.0f;")],
+    "quantisation scale 1023": [("height_axis ? 32768.0f : 1024.0f;",
+                                 "height_axis ? 32768.0f : 1023.0f;")],
     "split after the last equal prefix": [("if (clz64(K[f] ^ K[k]) > dfl) g = k;",
                                            "if (clz64(K[f] ^ K[k]) >= dfl) g = k;")],
     "adjoint end weights swapped": [("gA[3 * i + k] = (1.0 - t) * (gpk + lam[k]);",

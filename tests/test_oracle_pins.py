@@ -392,6 +392,47 @@ def test_lbvh_quantisation_against_float32_numpy(orc):
     np.testing.assert_array_equal(o["order"], np.lexsort((np.arange(len(codes)), codes)))
 
 
+def test_morton2_interleave_known_values(orc):
+    # height-field variant: first kept axis on the odd bits, 15 bits each
+    assert orc.morton2(1, 0) == 2
+    assert orc.morton2(0, 1) == 1
+    assert orc.morton2(3, 0) == 2 + 8
+    assert orc.morton2(0, 32767) == int("01" * 15, 2)
+    assert orc.morton2(32767, 32767) == (1 << 30) - 1
+    assert orc.morton2(16384, 0) == 1 << 29
+
+
+@pytest.mark.parametrize("height_axis", [1, 2, 3])
+def test_lbvh_height_axis_codes_against_float32_numpy(orc, height_axis):
+    """The height-field option of the code: the coordinate along the height
+    axis left out, the other two quantised to 2^15 levels (float32, as in
+    the paper's quantisation) and interleaved bit by bit, first kept axis
+    high; order by (code, index) and the radix tree as for the paper's code."""
+    mesh, _ = synth.workload_small_bool()
+    o = orc.lbvh(mesh.V, mesh.T, height_axis=height_axis)
+    P = mesh.V[mesh.T]
+    c = ((P[:, 0] + P[:, 1]) + P[:, 2]) / np.float32(3)
+    lo, hi = c.min(0), c.max(0)
+    q = np.clip(np.floor(((c - lo) / (hi - lo)) * np.float32(32768)), 0, 32767).astype(np.uint32)
+    a, b = [k for k in range(3) if k != height_axis - 1]
+    codes = np.zeros(len(q), np.uint32)
+    for k in range(15):
+        codes |= ((q[:, a] >> k) & 1) << (2 * k + 1)
+        codes |= ((q[:, b] >> k) & 1) << (2 * k)
+    np.testing.assert_array_equal(o["codes"], codes)
+    np.testing.assert_array_equal(o["order"], np.lexsort((np.arange(len(codes)), codes)))
+    keys = [(int(x) << 32) | i for i, x in enumerate(codes[o["order"]])]
+    want = _trie_tree(keys)
+    got = {}
+    for node in range(len(codes) - 1):
+        f, l = o["range"][node]
+        L = o["left"][node]
+        got[(int(f), int(l))] = int((-L - 1) if L < 0 else o["range"][L][1])
+    assert got == want
+    with pytest.raises(ValueError):
+        orc.lbvh(mesh.V, mesh.T, height_axis=4)
+
+
 def test_golden_cube_parity(orc):
     """tests/golden/cube_inside_cases.txt: the crossing count of a segment
     from each point along (0.31, 0.57, 0.76), 10 long, is odd exactly for
