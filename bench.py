@@ -269,6 +269,30 @@ def run_ours(args):
                         args.steps, stream, torch)
         ms_build = timed(lambda: bvh.build(V, T, stream=stream), args.steps, stream, torch)
         stats = bvh.intersect(A, B, "bool", stats=True, stream=stream)["stats"]
+        # the same step with the build's height-field option (the terrain is
+        # z = f(x, y): the Morton code leaves z out); the flags must not change
+        bvh_h = rsi.BVH(V, T, height_axis=3, stream=stream)
+        out_h = {"flag": torch.empty_like(out["flag"])}
+
+        def step_h():
+            bvh_h.build(V, T, stream=stream)
+            bvh_h.intersect(A, B, "bool", out=out_h, stream=stream)
+
+        step_h()
+        run_h = step_h
+        if not args.no_graph:
+            g_h = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g_h, stream=stream):
+                step_h()
+            run_h = g_h.replay
+        run_h()
+        ms_step_h = timed(run_h, args.steps, stream, torch)
+        ms_trav_h = timed(lambda: bvh_h.intersect(A, B, "bool", out=out_h, stream=stream),
+                          args.steps, stream, torch)
+        stats_h = bvh_h.intersect(A, B, "bool", stats=True, stream=stream)["stats"]
+        stream.synchronize()
+        if not torch.equal(out_h["flag"], out["flag"]):
+            raise RuntimeError("height-field tree gave other flags")
         # the FP32 ceiling, measured by the library's FMA probe (~60 ms)
         fp32_tflops = rsi.fp32_peak(1 << 20, stream=stream)
 
@@ -350,7 +374,15 @@ def run_ours(args):
                       "build_ms": round(ms_build, 4), "traverse_ms": round(ms_trav, 4),
                       "node_visits_per_seg": round(stats["node_visits"] / n_seg, 3),
                       "tri_tests_per_seg": round(stats["tri_tests"] / n_seg, 3),
-                      "fp64_tests_per_seg": stats["fp64_tests"] / n_seg},
+                      "fp64_tests_per_seg": stats["fp64_tests"] / n_seg,
+                      "height_axis_option": {
+                          "note": "the same step with the build option height_axis=3 (the "
+                                  "Morton code of the z = f(x, y) terrain leaves z out; same "
+                                  "flags); not the paper's code, so not the headline",
+                          "Msegs": round(n_seg / (ms_step_h * 1e-3) / 1e6, 3),
+                          "ms_per_step": round(ms_step_h, 4),
+                          "traverse_ms": round(ms_trav_h, 4),
+                          "node_visits_per_seg": round(stats_h["node_visits"] / n_seg, 3)}},
     }
     res.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -492,6 +524,43 @@ def run_extras(args, torch, rsi, synth, dev, stream, dist=None):
             stream.synchronize()
             ms_ord[name] = timed(g_o.replay, steps, stream, torch)
             del g_o
+        # the same steps over a tree built with the height-field option (the
+        # terrain is z = f(x, y): the Morton code leaves z out); same outputs
+        bvh_h = rsi.BVH(V, T, height_axis=3, stream=stream)
+        order_h = bvh_h.segment_order(A, B, stream=stream)
+        lo_h = {"order": order_h}
+
+        def fwd_bwd_h():
+            bvh_h.build(V, T, stream=stream)
+            o = bvh_h.intersect(A, B, "nearest", stream=stream)
+            rsi.intersect_backward(V, T, A, B, o["tri"], grad_point=W, stream=stream)
+
+        def fwd_bwd_h_refit_ordered():
+            bvh_h.refit(V, stream=stream)
+            o = bvh_h.intersect(A, B, "nearest", launch=lo_h, stream=stream)
+            rsi.intersect_backward(V, T, A, B, o["tri"], grad_point=W, stream=stream)
+
+        for name, fn in (("h_build", fwd_bwd_h), ("h_refit_order", fwd_bwd_h_refit_ordered)):
+            fn()
+            g_o = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g_o, stream=stream):
+                fn()
+            g_o.replay()
+            stream.synchronize()
+            ms_ord[name] = timed(g_o.replay, steps, stream, torch)
+            del g_o
+        o_h = bvh_h.intersect(A, B, "nearest", stream=stream)
+        ms_near_h = timed(lambda: bvh_h.intersect(A, B, "nearest", out=o_h, stream=stream),
+                          steps, stream, torch)
+        ms_near_h_ord = timed(lambda: bvh_h.intersect(A, B, "nearest", launch=lo_h, out=o_h,
+                                                      stream=stream), steps, stream, torch)
+        st_h = bvh_h.intersect(A, B, "nearest", stats=True, stream=stream)["stats"]
+        o_ref = bvh.intersect(A, B, "nearest", stream=stream)
+        stream.synchronize()
+        for k in ("tri", "tuv", "point", "dist"):
+            if not torch.equal(o_h[k], o_ref[k]):
+                raise RuntimeError("height-field tree gave other nearest outputs")
+        del bvh_h
         o_in = bvh.intersect(A, B, "nearest", stream=stream)
         o_ord = bvh.intersect(A, B, "nearest", launch=lo_ord, stream=stream)
         ms_near_in = timed(lambda: bvh.intersect(A, B, "nearest", out=o_in, stream=stream),
@@ -525,6 +594,16 @@ def run_extras(args, torch, rsi, synth, dev, stream, dist=None):
                           "nearest_ms": {"input_order": round(ms_near_in, 4),
                                          "segment_order": round(ms_near_ord, 4),
                                          "computing_the_order": round(ms_order, 4)},
+                          "height_axis_option": {
+                              "note": "the tree built with height_axis=3 (the terrain's "
+                                      "Morton code leaves z out; same outputs); not the "
+                                      "paper's code",
+                              "graph": round(seg.n / (ms_ord["h_build"] * 1e-3) / 1e6, 3),
+                              "with_refit_order_graph": round(
+                                  seg.n / (ms_ord["h_refit_order"] * 1e-3) / 1e6, 3),
+                              "nearest_ms": {"input_order": round(ms_near_h, 4),
+                                             "segment_order": round(ms_near_h_ord, 4)},
+                              "node_visits_per_seg": round(st_h["node_visits"] / seg.n, 3)},
                           "nearest_breakdown": {
                               "node_visits_per_seg": round(st["node_visits"] / seg.n, 3),
                               "tri_tests_per_seg": round(st["tri_tests"] / seg.n, 3),

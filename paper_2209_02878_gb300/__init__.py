@@ -181,16 +181,21 @@ def _rsi_output(o) -> _abi.rsi_output:
 
 class BVH:
     """LBVH of one indexed triangle mesh on the current CUDA device
-    (rsi_bvh_create + rsi_bvh_build).  V: float32 [nV,3], T: int32 [nT,3]."""
+    (rsi_bvh_create + rsi_bvh_build).  V: float32 [nV,3], T: int32 [nT,3].
+    height_axis: 0 for the paper's Morton code over x, y, z; 1, 2 or 3 for a
+    mesh that is a height field along that axis (a terrain z = f(x, y): 3),
+    whose code then leaves that coordinate out (same results, a tree better
+    suited to the surface)."""
 
-    def __init__(self, V, T, leaf_size: int = 0, top_levels: int = 0, stream=None):
+    def __init__(self, V, T, leaf_size: int = 0, top_levels: int = 0, stream=None,
+                 height_axis: int = 0):
         self._lib = _abi.load()
         _check_tensor(V, "V", torch.float32)
         _check_tensor(T, "T", torch.int32)
         self.nV, self.nT = int(V.shape[0]), int(T.shape[0])
         self.device = V.device
-        self.leaf_size, self.top_levels = leaf_size, top_levels
-        opts = _abi.rsi_build_opts(int(leaf_size), int(top_levels))
+        self.leaf_size, self.top_levels, self.height_axis = leaf_size, top_levels, height_axis
+        opts = _abi.rsi_build_opts(int(leaf_size), int(top_levels), int(height_axis))
         h = C.c_void_p()
         with torch.cuda.device(self.device):
             _abi.check(self._lib.rsi_bvh_create(self.nV, self.nT, C.byref(opts), _stream(stream),
@@ -385,7 +390,8 @@ class BVH:
 
 def intersect(V, T, A, B, mode="bool", **kw):
     """Build a BVH for (V, T) and test the segments (one-shot convenience)."""
-    bvh = BVH(V, T, leaf_size=kw.pop("leaf_size", 0), top_levels=kw.pop("top_levels", 0))
+    bvh = BVH(V, T, leaf_size=kw.pop("leaf_size", 0), top_levels=kw.pop("top_levels", 0),
+              height_axis=kw.pop("height_axis", 0))
     try:
         return bvh.intersect(A, B, mode, **kw)
     finally:
@@ -462,9 +468,11 @@ def nearest_hit(V, T, A, B, bvh=None, order=None):
 class Batch:
     """Many independent (mesh, segments, mode) problems: one multi-mesh build
     and one persistent traversal launch, optionally replayed as a CUDA graph
-    (rsi_batch_create / _build / _intersect / _run_graph)."""
+    (rsi_batch_create / _build / _intersect / _run_graph).  height_axis as
+    for BVH, for every mesh of the batch."""
 
-    def __init__(self, items, leaf_size=0, launch=None, compact=False, stream=None):
+    def __init__(self, items, leaf_size=0, launch=None, compact=False, stream=None,
+                 height_axis=0):
         self._lib = _abi.load()
         self.items = []
         self.outputs = []
@@ -483,7 +491,7 @@ class Batch:
             it.dA, it.dB, it.nR, it.mode = A.data_ptr(), B.data_ptr(), A.shape[0], m
             it.out = _rsi_output(o)
         self._arr = arr
-        bo = _abi.rsi_build_opts(int(leaf_size), 0)
+        bo = _abi.rsi_build_opts(int(leaf_size), 0, int(height_axis))
         lo = _launch(launch)
         h = C.c_void_p()
         _abi.check(self._lib.rsi_batch_create(arr, len(items), C.byref(bo), C.byref(lo),

@@ -37,7 +37,7 @@ i64 = C.c_int64
 
 
 class rsi_build_opts(C.Structure):
-    _fields_ = [("leaf_size", i32), ("top_levels", i32)]
+    _fields_ = [("leaf_size", i32), ("top_levels", i32), ("height_axis", i32)]
 
 
 # rsi_alloc_fn / rsi_free_fn (pass as c_void_p after ctypes.cast)

@@ -75,12 +75,16 @@ size_t carve(TreeBufs& tb, int64_t N, int M, int nblk, char* base) {
     return off;
 }
 
-rsi_status check_build_opts(const rsi_build_opts* o, int32_t* leaf, int32_t* levels) {
+rsi_status check_build_opts(const rsi_build_opts* o, int32_t* leaf, int32_t* levels,
+                            int32_t* height) {
     *leaf = 1;
     *levels = 0;
+    *height = 0;
     if (!o) return RSI_OK;
     if (o->leaf_size < 0 || o->leaf_size > rsi::kMaxLeaf) return RSI_ERR_ARG;
     if (o->top_levels < -1 || o->top_levels > 12) return RSI_ERR_ARG;
+    if (o->height_axis < 0 || o->height_axis > 3) return RSI_ERR_ARG;
+    *height = o->height_axis;
     if (o->leaf_size > 0) *leaf = o->leaf_size;
     if (o->top_levels > 0) *levels = o->top_levels;
     return RSI_OK;
@@ -253,8 +257,8 @@ rsi_status rsi_bvh_create(int64_t nV, int64_t nT, const rsi_build_opts* opt, rsi
     if (!out) return RSI_ERR_ARG;
     *out = nullptr;
     if (nV < 0 || nT < 0 || nT >= (int64_t)1 << 31) return RSI_ERR_ARG;
-    int32_t leaf, levels;
-    rsi_status st = check_build_opts(opt, &leaf, &levels);
+    int32_t leaf, levels, height;
+    rsi_status st = check_build_opts(opt, &leaf, &levels, &height);
     if (st != RSI_OK) return st;
     int device = 0;
     RSI_CK(cudaGetDevice(&device));
@@ -280,6 +284,7 @@ rsi_status rsi_bvh_create(int64_t nV, int64_t nT, const rsi_build_opts* opt, rsi
     carve(tb, nT, 1, nblk, h->mem);
     h->scratch = (unsigned long long*)(h->mem + bytes - 256);
     tb.leaf_size = leaf;
+    tb.height_axis = height;
     tb.top_levels = levels;
     tb.sorted = 0;
     h->tb = tb;
@@ -922,8 +927,8 @@ rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_bu
                             const rsi_launch_opts* lo, rsi_stream s, rsi_batch* out) {
     if (!out || n < 1 || !items) return RSI_ERR_ARG;
     *out = nullptr;
-    int32_t leaf, levels;
-    rsi_status st = check_build_opts(bo, &leaf, &levels);
+    int32_t leaf, levels, height;
+    rsi_status st = check_build_opts(bo, &leaf, &levels, &height);
     if (st != RSI_OK) return st;
     LaunchCfg cfg;
     st = check_launch_opts(lo, false, &cfg);
@@ -1010,6 +1015,7 @@ rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_bu
     }
     carve(tb, N, n, nblk, b->mem);
     tb.leaf_size = leaf;
+    tb.height_axis = height;
     tb.top_levels = 0;
     b->tb = tb;
     b->bytes = bytes;

@@ -5,6 +5,8 @@
 //   a2  k_morton            : q = clamp(floor(((c - lo) / (hi - lo)) 1024),
 //                             0, 1023), 30-bit Morton code, sort key
 //                             mesh << 32 | code, value = triangle index
+//                             (option height_axis: that axis left out, the
+//                             other two quantised to 2^15 levels)
 //   a3  k_sort_*            : stable LSD radix sort, 8-bit digits
 //   a4  k_karras            : binary radix tree over the distinct keys
 //                             code << 32 | sorted position (Karras 2012, as
@@ -122,13 +124,26 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x) {
     return x;
 }
 
-__device__ __forceinline__ uint32_t quant(float c, float lo, float hi) {
+// q = clamp(floor(((c - lo) / (hi - lo)) * levels), 0, levels - 1); 0 for a
+// zero extent (levels = 1024 for the paper's code, 2^15 for the height-field
+// option's two axes).
+__device__ __forceinline__ uint32_t quant(float c, float lo, float hi, float levels) {
     const float ext = __fsub_rn(hi, lo);
     if (!(ext > 0.f)) return 0u;
-    float s = __fmul_rn(__fdiv_rn(__fsub_rn(c, lo), ext), 1024.0f);
+    float s = __fmul_rn(__fdiv_rn(__fsub_rn(c, lo), ext), levels);
     s = floorf(s);
-    s = fminf(fmaxf(s, 0.f), 1023.f);
+    s = fminf(fmaxf(s, 0.f), levels - 1.f);
     return (uint32_t)s;
+}
+
+// 15-bit x -> bit k at bit 2k.
+__device__ __forceinline__ uint32_t spread2(uint32_t x) {
+    x &= 0x7fffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
 }
 
 // a2: mesh interval from the partials, quantisation, Morton code, sort key.
@@ -155,10 +170,18 @@ __global__ void __launch_bounds__(kBuildThreads) k_morton(MeshArgs ma, TreeBufs 
         uint32_t code = 0;
         if (tri_vertices(md, j, tb.status, a, bb, c)) {
             const float3 ce = centroid(a, bb, c);
-            if (finite3(ce.x, ce.y, ce.z))
-                code = (spread3(quant(ce.x, bnd[0], bnd[3])) << 2) |
-                       (spread3(quant(ce.y, bnd[1], bnd[4])) << 1) |
-                       spread3(quant(ce.z, bnd[2], bnd[5]));
+            if (finite3(ce.x, ce.y, ce.z)) {
+                if (tb.height_axis == 0) {
+                    code = (spread3(quant(ce.x, bnd[0], bnd[3], 1024.f)) << 2) |
+                           (spread3(quant(ce.y, bnd[1], bnd[4], 1024.f)) << 1) |
+                           spread3(quant(ce.z, bnd[2], bnd[5], 1024.f));
+                } else {  // height field: the other two axes, the first one high
+                    const float cc[3] = {ce.x, ce.y, ce.z};
+                    const int a = tb.height_axis == 1 ? 1 : 0, b = tb.height_axis == 3 ? 1 : 2;
+                    code = (spread2(quant(cc[a], bnd[a], bnd[3 + a], 32768.f)) << 1) |
+                           spread2(quant(cc[b], bnd[b], bnd[3 + b], 32768.f));
+                }
+            }
         }
         tb.keys[0][md.off + j] = ((uint64_t)m << 32) | code;
         tb.vals[0][md.off + j] = (uint32_t)(md.off + j);

@@ -110,6 +110,7 @@ struct TreeBufs {
     int32_t* treelet_n;
     int32_t* status;  // device status word (rsi_status)
     int32_t leaf_size;
+    int32_t height_axis;  // 0: Morton code over x, y, z; 1..3: that axis left out
     int32_t top_levels;  // < 0: no treelet
     int32_t sorted;      // which keys/vals buffer holds the sorted result
 };
