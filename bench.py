@@ -224,7 +224,9 @@ def run_ours(args):
         bvh = rsi.BVH(V, T, stream=stream)
         # build: bounds, Morton, 4 sort passes x (histogram, scatter; the scan
         # is folded into the scatter at 30 tiles), Karras, climb; + traversal
-        kernels_per_step = 2 + 2 * 4 + 1 + 1 + 1
+        # bounds, Morton, 4 x (histogram, scatter), Karras, the two box
+        # passes, the traversal
+        kernels_per_step = 2 + 2 * 4 + 1 + 2 + 1
 
         def eager_step():
             bvh.build(V, T, stream=stream)
@@ -235,7 +237,7 @@ def run_ours(args):
         stream.synchronize()
         step = eager_step
         if not args.no_graph:
-            # the whole step (build + traversal, 13 kernels) as one CUDA graph
+            # the whole step (build + traversal, 14 kernels) as one CUDA graph
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, stream=stream):
                 eager_step()
