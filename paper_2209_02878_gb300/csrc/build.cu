@@ -203,7 +203,7 @@ __global__ void k_karras(MeshArgs ma, TreeBufs tb, const uint64_t* __restrict__ 
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= tb.N) return;
     const MeshDesc md = mesh_of(ma, (int)(keys[g] >> 32));
-    const int off = md.off, n = md.n, i = g - off, N = tb.N;
+    const int off = md.off, n = md.n, i = g - off;
     if (g == 0) *tb.nspan = 0;  // the box pass lists the slots that span its blocks
     if (i == n - 1) return;  // root slot of this mesh
     const int d = kdelta(keys, off, n, i, i + 1) > kdelta(keys, off, n, i, i - 1) ? 1 : -1;
