@@ -150,9 +150,8 @@ __device__ __forceinline__ float2 up2(unsigned long long r) {
     return v;
 }
 __device__ __forceinline__ float lo32(unsigned long long r) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-    (void)b;
+    float a;
+    asm("{\n\t.reg .b32 hi;\n\tmov.b64 {%0, hi}, %1;\n\t}" : "=f"(a) : "l"(r));
     return a;
 }
 
