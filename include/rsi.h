@@ -528,6 +528,21 @@ rsi_status rsi_autotune(rsi_bvh h, const float* dV, const int32_t* dT,
                         rsi_stream s, rsi_tune_entry* table, int32_t cap,
                         int32_t* n_written, rsi_launch_opts* best_lo, int32_t* best_leaf);
 
+/* Autotuner for the build option height_axis (not in the paper): rebuilds h
+ * from dV, dT with each of the Morton codes 0 (x, y, z), 1, 2, 3 (that axis
+ * left out), times `reps` traversals of the given segments in `mode` with
+ * launch options lo (NULL = defaults) under each (median, CUDA events on s),
+ * writes the four medians to ms[4] (host) and the fastest axis to
+ * *best_axis, and leaves h built with it (its later builds and refits keep
+ * it).  Results never depend on the choice.  Synchronous.  Errors:
+ * RSI_ERR_ARG (NULL pointer, nR <= 0, reps < 1), RSI_ERR_NOT_BUILT, and
+ * those of rsi_bvh_build / rsi_intersect. */
+rsi_status rsi_autotune_height_axis(rsi_bvh h, const float* dV, const int32_t* dT,
+                                    const float* dA, const float* dB, int64_t nR,
+                                    rsi_mode mode, const rsi_output* out,
+                                    const rsi_launch_opts* lo, int32_t reps, rsi_stream s,
+                                    float* ms, int32_t* best_axis);
+
 /* --------------------------------------------------------- measurement --- */
 
 /* FP32 peak probe (not part of the paper's method): launches an FMA-only

@@ -107,6 +107,9 @@ _PROTOS = {
     "rsi_batch_intersect": (C.c_int, [vp, vp]),
     "rsi_batch_run_graph": (C.c_int, [vp, i32, vp]),
     "rsi_batch_destroy": (C.c_int, [vp]),
+    "rsi_autotune_height_axis": (C.c_int, [vp, vp, vp, vp, vp, i64, C.c_int, P(rsi_output),
+                                           P(rsi_launch_opts), i32, vp, P(C.c_float),
+                                           P(i32)]),
     "rsi_autotune": (C.c_int, [vp, vp, vp, vp, vp, i64, C.c_int, P(rsi_output),
                                P(i32), i32, P(i32), i32, P(i32), i32, P(i32), i32, i32, vp,
                                P(rsi_tune_entry), i32, P(i32), P(rsi_launch_opts), P(i32)]),

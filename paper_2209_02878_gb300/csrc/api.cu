@@ -1212,4 +1212,49 @@ rsi_status rsi_autotune(rsi_bvh h, const float* dV, const int32_t* dT, const flo
     return result;
 }
 
+rsi_status rsi_autotune_height_axis(rsi_bvh h, const float* dV, const int32_t* dT,
+                                    const float* dA, const float* dB, int64_t nR,
+                                    rsi_mode mode, const rsi_output* out,
+                                    const rsi_launch_opts* lo, int32_t reps, rsi_stream s,
+                                    float* ms, int32_t* best_axis) {
+    if (!h || !dV || !dT || !dA || !dB || !out || !ms || !best_axis || nR <= 0 || reps < 1)
+        return RSI_ERR_ARG;
+    if (!h->built) return RSI_ERR_NOT_BUILT;
+    cudaStream_t cs = (cudaStream_t)s;
+    cudaEvent_t e0, e1;
+    RSI_CK(cudaEventCreate(&e0));
+    RSI_CK(cudaEventCreate(&e1));
+    const int32_t axis0 = h->tb.height_axis;
+    *best_axis = axis0;
+    float best_ms = INFINITY;
+    rsi_status result = RSI_OK;
+    for (int a = 0; a < 4 && result == RSI_OK; ++a) {
+        h->tb.height_axis = a;
+        result = rsi_bvh_build(h, dV, dT, s);
+        if (result == RSI_OK) result = rsi_intersect(h, dA, dB, nR, mode, out, lo, s);  // warm-up
+        std::vector<float> t(reps);
+        for (int r = 0; r < reps && result == RSI_OK; ++r) {
+            cudaEventRecord(e0, cs);
+            result = rsi_intersect(h, dA, dB, nR, mode, out, lo, s);
+            cudaEventRecord(e1, cs);
+            if (cudaEventSynchronize(e1) != cudaSuccess) result = RSI_ERR_CUDA;
+            cudaEventElapsedTime(&t[r], e0, e1);
+        }
+        if (result != RSI_OK) break;
+        std::sort(t.begin(), t.end());
+        ms[a] = t[reps / 2];
+        if (ms[a] < best_ms) {
+            best_ms = ms[a];
+            *best_axis = a;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->tb.height_axis = result == RSI_OK ? *best_axis : axis0;
+    const rsi_status rb = rsi_bvh_build(h, dV, dT, s);
+    if (result == RSI_OK) result = rb;
+    if (result == RSI_OK && cudaStreamSynchronize(cs) != cudaSuccess) result = RSI_ERR_CUDA;
+    return result;
+}
+
 }  // extern "C"

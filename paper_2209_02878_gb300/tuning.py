@@ -1,6 +1,7 @@
 """Autotuner front end: runs rsi_autotune (the timing loop lives in the
 library) and keeps a JSON cache keyed by (GPU name, mode, N_t bucket, N_r
-bucket), so a workload class is tuned once per GPU model."""
+bucket), so a workload class is tuned once per GPU model; and
+rsi_autotune_height_axis, which picks the build's Morton axes for a mesh."""
 from __future__ import annotations
 
 import ctypes as C
@@ -32,6 +33,28 @@ def _load(path):
             return json.load(f)
     except (OSError, ValueError):
         return {}
+
+
+def autotune_height_axis(bvh, V, T, A, B, mode="bool", launch=None, reps=5, stream=None):
+    """Time the traversal of these segments over trees built with each
+    Morton code (height_axis 0: x, y, z; 1, 2, 3: that axis left out) and
+    leave bvh built with the fastest.  Returns (best axis, {axis: ms})."""
+    from . import _launch
+    lib = _abi.load()
+    m = _mode(mode)
+    n = int(A.shape[0])
+    o = _alloc_outputs(m, n, A.device, False, None)
+    ro = _rsi_output(o)
+    lo = _launch(launch, n, A.device)
+    ms = (C.c_float * 4)()
+    best = C.c_int32()
+    with torch.cuda.device(A.device):
+        _abi.check(lib.rsi_autotune_height_axis(bvh._h, _vp(V), _vp(T), _vp(A), _vp(B), n, m,
+                                                C.byref(ro), C.byref(lo), int(reps),
+                                                _stream(stream), ms, C.byref(best)),
+                   "rsi_autotune_height_axis")
+    bvh.height_axis = best.value
+    return best.value, {a: float(ms[a]) for a in range(4)}
 
 
 def autotune(bvh, V, T, A, B, mode="bool", block_sizes=(64, 128, 256, 512),

@@ -101,3 +101,22 @@ def test_bad_height_axis_is_refused(small):
     mesh, _, _ = small
     with pytest.raises(Exception):
         rsi.BVH(dev(mesh.V), dev(mesh.T), height_axis=4)
+
+
+def test_autotuner_picks_the_height_axis():
+    from paper_2209_02878_gb300 import tuning
+    mesh, seg, _ = synth.workload_diff(seed=12, n_seg=100_000)
+    V, T, A, B = dev(mesh.V), dev(mesh.T), dev(seg.A), dev(seg.B)
+    bvh = rsi.BVH(V, T)
+    base = bvh.intersect(A, B, "nearest")
+    best, ms = tuning.autotune_height_axis(bvh, V, T, A, B, "nearest", reps=5)
+    assert best == 3, ms  # a terrain z = f(x, y): leaving z out is clearly fastest
+    assert ms[3] < 0.8 * ms[0], ms
+    assert bvh.height_axis == 3
+    got = bvh.intersect(A, B, "nearest")  # the handle stays built with axis 3
+    torch.cuda.synchronize()
+    for k in ("tri", "tuv", "point", "dist"):
+        assert torch.equal(got[k], base[k]), k
+    g = bvh.export()
+    r = oracle.lbvh(mesh.V, mesh.T, height_axis=3)
+    np.testing.assert_array_equal(g["left"], r["left"])
