@@ -468,7 +468,9 @@ typedef struct {
     const float* dB;
     int64_t nR;
     int32_t mode;   /* rsi_mode */
-    int32_t pad;
+    int32_t height_axis; /* 1, 2, 3: this mesh's Morton code leaves that axis
+                            out (rsi_build_opts.height_axis, per item); 0:
+                            the batch's build option */
     rsi_output out;
 } rsi_batch_item;
 

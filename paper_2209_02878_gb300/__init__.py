@@ -468,8 +468,9 @@ def nearest_hit(V, T, A, B, bvh=None, order=None):
 class Batch:
     """Many independent (mesh, segments, mode) problems: one multi-mesh build
     and one persistent traversal launch, optionally replayed as a CUDA graph
-    (rsi_batch_create / _build / _intersect / _run_graph).  height_axis as
-    for BVH, for every mesh of the batch."""
+    (rsi_batch_create / _build / _intersect / _run_graph).  Items are
+    (V, T, A, B, mode) or (V, T, A, B, mode, height_axis); height_axis as for
+    BVH, per item, or for every item without its own."""
 
     def __init__(self, items, leaf_size=0, launch=None, compact=False, stream=None,
                  height_axis=0):
@@ -477,7 +478,9 @@ class Batch:
         self.items = []
         self.outputs = []
         arr = (_abi.rsi_batch_item * len(items))()
-        for k, (V, T, A, B, mode) in enumerate(items):
+        for k, item in enumerate(items):
+            V, T, A, B, mode = item[:5]
+            item_axis = int(item[5]) if len(item) > 5 else 0
             _check_tensor(V, "V", torch.float32)
             _check_tensor(T, "T", torch.int32)
             _check_tensor(A, "A", torch.float32)
@@ -489,6 +492,7 @@ class Batch:
             it = arr[k]
             it.dV, it.nV, it.dT, it.nT = V.data_ptr(), V.shape[0], T.data_ptr(), T.shape[0]
             it.dA, it.dB, it.nR, it.mode = A.data_ptr(), B.data_ptr(), A.shape[0], m
+            it.height_axis = item_axis
             it.out = _rsi_output(o)
         self._arr = arr
         bo = _abi.rsi_build_opts(int(leaf_size), 0, int(height_axis))

@@ -69,7 +69,7 @@ class rsi_stats(C.Structure):
 
 class rsi_batch_item(C.Structure):
     _fields_ = [("dV", vp), ("nV", i64), ("dT", vp), ("nT", i64), ("dA", vp), ("dB", vp),
-                ("nR", i64), ("mode", i32), ("pad", i32), ("out", rsi_output)]
+                ("nR", i64), ("mode", i32), ("height_axis", i32), ("out", rsi_output)]
 
 
 class rsi_tune_entry(C.Structure):

@@ -315,6 +315,7 @@ rsi_status rsi_bvh_build(rsi_bvh h, const float* dV, const int32_t* dT, rsi_stre
     ma.one.off = 0;
     ma.one.blk0 = 0;
     ma.one.nblk = h->tb.nblk;
+    ma.one.height_axis = h->tb.height_axis;
     h->tb.leaf_size = h->leaf;
     h->tb.top_levels = h->levels;
     RSI_CK(rsi::build_tree(h->tb, ma, (cudaStream_t)s, false));
@@ -955,6 +956,8 @@ rsi_status rsi_batch_create(const rsi_batch_item* items, int32_t n, const rsi_bu
         md.off = (int32_t)N;
         md.blk0 = nblk;
         md.nblk = (int32_t)((it.nT + rsi::kBuildChunk - 1) / rsi::kBuildChunk);
+        if (it.height_axis < 0 || it.height_axis > 3) return RSI_ERR_ARG;
+        md.height_axis = it.height_axis > 0 ? it.height_axis : height;
         for (int q = 0; q < md.nblk; ++q) blkmesh.push_back(k);
         nblk += md.nblk;
         N += it.nT;
@@ -1061,6 +1064,7 @@ static MeshArgs batch_mesh_args(rsi_batch b) {
         ma.one.nV = it.nV;
         ma.one.n = (int32_t)it.nT;
         ma.one.nblk = b->tb.nblk;
+        ma.one.height_axis = it.height_axis > 0 ? it.height_axis : b->tb.height_axis;
     }
     return ma;
 }

@@ -171,13 +171,13 @@ __global__ void __launch_bounds__(kBuildThreads) k_morton(MeshArgs ma, TreeBufs 
         if (tri_vertices(md, j, tb.status, a, bb, c)) {
             const float3 ce = centroid(a, bb, c);
             if (finite3(ce.x, ce.y, ce.z)) {
-                if (tb.height_axis == 0) {
+                if (md.height_axis == 0) {
                     code = (spread3(quant(ce.x, bnd[0], bnd[3], 1024.f)) << 2) |
                            (spread3(quant(ce.y, bnd[1], bnd[4], 1024.f)) << 1) |
                            spread3(quant(ce.z, bnd[2], bnd[5], 1024.f));
                 } else {  // height field: the other two axes, the first one high
                     const float cc[3] = {ce.x, ce.y, ce.z};
-                    const int a = tb.height_axis == 1 ? 1 : 0, b = tb.height_axis == 3 ? 1 : 2;
+                    const int a = md.height_axis == 1 ? 1 : 0, b = md.height_axis == 3 ? 1 : 2;
                     code = (spread2(quant(cc[a], bnd[a], bnd[3 + a], 32768.f)) << 1) |
                            spread2(quant(cc[b], bnd[b], bnd[3 + b], 32768.f));
                 }

@@ -69,6 +69,7 @@ struct MeshDesc {
     int32_t off;   // offset in concatenated triangle / node arrays
     int32_t blk0;  // first block of this mesh in the bounds / Morton grid
     int32_t nblk;
+    int32_t height_axis;  // Morton code: 0 over x, y, z; 1..3 that axis left out
 };
 
 struct MeshArgs {
@@ -110,7 +111,7 @@ struct TreeBufs {
     int32_t* treelet_n;
     int32_t* status;  // device status word (rsi_status)
     int32_t leaf_size;
-    int32_t height_axis;  // 0: Morton code over x, y, z; 1..3: that axis left out
+    int32_t height_axis;  // the handle's Morton option (copied into each MeshDesc)
     int32_t top_levels;  // < 0: no treelet
     int32_t sorted;      // which keys/vals buffer holds the sorted result
 };

@@ -120,3 +120,28 @@ def test_autotuner_picks_the_height_axis():
     g = bvh.export()
     r = oracle.lbvh(mesh.V, mesh.T, height_axis=3)
     np.testing.assert_array_equal(g["left"], r["left"])
+
+
+def test_batch_per_item_height_axis():
+    # terrains with the option, icospheres without, in one batch
+    rng = np.random.default_rng(6)
+    items, refs = [], []
+    for k, G in enumerate((33, 50)):
+        mesh = synth.heightfield(G, rng)
+        seg = synth.segments_random_direction(rng, 4000, mesh.V)
+        V, T, A, B = dev(mesh.V), dev(mesh.T), dev(seg.A), dev(seg.B)
+        items.append((V, T, A, B, "count", 3))
+        refs.append(rsi.BVH(V, T).intersect(A, B, "count")["count"])
+        sph = synth.icosphere(3 + k, rng)
+        sseg = synth.segments_box(rng, 4000, [-1.5] * 3, [1.5] * 3, [-1.5] * 3, [1.5] * 3)
+        V, T, A, B = dev(sph.V), dev(sph.T), dev(sseg.A), dev(sseg.B)
+        items.append((V, T, A, B, "count"))
+        refs.append(rsi.BVH(V, T).intersect(A, B, "count")["count"])
+    batch = rsi.Batch(items)
+    outs = batch.run_graph()
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    for o, r in zip(outs, refs):
+        assert torch.equal(o["count"], r)
+    with pytest.raises(Exception):
+        rsi.Batch([items[0][:5] + (5,)])
