@@ -77,8 +77,9 @@ typedef enum {
     RSI_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
     RSI_ERR_NOT_BUILT = 7,      /* handle has no built tree */
     RSI_ERR_INTERNAL = 8,       /* a device-side consistency bound was hit (a
-                                   climb longer than any radix tree, or more
-                                   node visits than nodes); the work stopped */
+                                   tree slot or leaf range out of its mesh,
+                                   or more node visits than nodes); the work
+                                   stopped */
     RSI_ERR_CAPACITY = 9        /* the problem exceeds the fixed scratch of an
                                    allocation-free entry point */
 } rsi_status;

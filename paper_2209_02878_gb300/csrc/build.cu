@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(128) k_boxes_span(MeshArgs ma, TreeBufs tb,
 }
 
 // 4-wide records for every slot of the built tree (one thread per slot, after
-// the climb has written all binary records).  Only needed by 4-wide
+// the box passes have written all binary records).  Only needed by 4-wide
 // traversal, so it runs on first use.
 __global__ void k_nodes4(const float4* __restrict__ nodes, float4* __restrict__ nodes4, int N) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
