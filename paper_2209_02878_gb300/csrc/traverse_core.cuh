@@ -590,6 +590,7 @@ __device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long
         // finished one run divergently, so wait until kRefillMin lanes are
         // free (or the whole warp is).
         if (__popc(idle) < kRefillMin && idle != FULL) idle = 0u;
+        const bool refill = idle != 0u;  // warp-uniform
         if (idle) {  // outputs of the finished segments first
             float dist = 0.f, P[3] = {0.f, 0.f, 0.f};
             if (done)
@@ -653,7 +654,8 @@ __device__ __forceinline__ void trace_loop(const TraceCtx& C, unsigned long long
             pool += avail;
             idle = __ballot_sync(FULL, i < 0);
         }
-        if (__ballot_sync(FULL, i >= 0) == 0u) break;
+        // without a refill some lane is still busy: the warp goes on
+        if (refill && __ballot_sync(FULL, i >= 0) == 0u) break;
         if (i >= 0 && !done) {
             bool overflow = false;
             if (W == 4)
