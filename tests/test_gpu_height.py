@@ -145,3 +145,36 @@ def test_batch_per_item_height_axis():
         assert torch.equal(o["count"], r)
     with pytest.raises(Exception):
         rsi.Batch([items[0][:5] + (5,)])
+
+
+@pytest.mark.parametrize("nT", [1, 2, 3, 17, 600])
+@pytest.mark.parametrize("axis", [1, 3])
+def test_height_axis_small_meshes(nT, axis):
+    rng = np.random.default_rng(nT + 10 * axis)
+    mesh, seg = synth.random_soup(rng, nT, 2000)
+    ref = oracle.brute(mesh.V, mesh.T, seg.A, seg.B)
+    bvh = rsi.BVH(dev(mesh.V), dev(mesh.T), height_axis=axis, leaf_size=2)
+    got = outputs(bvh, dev(seg.A), dev(seg.B))
+    np.testing.assert_array_equal(got["count"]["count"], ref["count"])
+    np.testing.assert_array_equal(got["nearest"]["tri"], ref["tri"])
+    tree_check(bvh.export(), nT, leaf_size=2)
+    if nT > 1:
+        r = oracle.lbvh(mesh.V, mesh.T, height_axis=axis)
+        g = bvh.export()
+        for k in ("left", "right", "range", "nbox", "lbox"):
+            np.testing.assert_array_equal(g[k], r[k], err_msg=k)
+
+
+def test_single_item_batch_with_height_axis():
+    rng = np.random.default_rng(21)
+    mesh = synth.heightfield(30, rng)
+    seg = synth.segments_random_direction(rng, 5000, mesh.V)
+    V, T, A, B = dev(mesh.V), dev(mesh.T), dev(seg.A), dev(seg.B)
+    ref = rsi.BVH(V, T).intersect(A, B, "nearest")
+    for item, batch_axis in (((V, T, A, B, "nearest", 3), 0), ((V, T, A, B, "nearest"), 3)):
+        b = rsi.Batch([item], height_axis=batch_axis)
+        out = b.run_graph()[0]
+        torch.cuda.synchronize()
+        for k in ("tri", "tuv", "point", "dist"):
+            assert torch.equal(out[k], ref[k]), k
+        b.close()

@@ -150,3 +150,26 @@ def test_nearest_hit_with_order_same_gradients(diff_case):
     # rounding of the FP64 sums
     g0, g1 = grads[0][2], grads[1][2]
     assert torch.allclose(g0, g1, rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("nT,nR", [(0, 5), (1, 1), (2, 33), (17, 1000)])
+def test_order_edge_sizes(nT, nR):
+    rng = np.random.default_rng(nT * 7 + nR)
+    if nT == 0:
+        V = np.zeros((3, 3), np.float32)
+        T = np.zeros((0, 3), np.int32)
+        A = rng.uniform(0, 1, (nR, 3)).astype(np.float32)
+        B = rng.uniform(0, 1, (nR, 3)).astype(np.float32)
+    else:
+        mesh, seg = synth.random_soup(rng, nT, nR)
+        V, T, A, B = mesh.V, mesh.T, seg.A, seg.B
+    bvh = rsi.BVH(t(V), t(T))
+    order = bvh.segment_order(t(A), t(B))
+    torch.cuda.synchronize()
+    assert torch.equal(torch.sort(order.long())[0], torch.arange(nR, device=DEV))
+    for mode in ("bool", "count", "nearest"):
+        ref = bvh.intersect(t(A), t(B), mode)
+        got = bvh.intersect(t(A), t(B), mode, launch={"order": order})
+        torch.cuda.synchronize()
+        _same(ref, got)
+    assert bvh.status() == 0
